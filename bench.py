@@ -1,0 +1,371 @@
+#!/usr/bin/env python3
+"""Benchmark: frames/s of the structure-function analysis of a synthetic NFS image sequence.
+
+Default workload: 4000 frames of 2048x2048 uint16 (12-bit counts from the seeded OU beam model),
+200 log-spaced delays 1..2000, 1024 radial q bins -- one "step" is the whole job: every frame
+through the exact mean, the r2c FFT into the spectrum ring, the fused delay update of Eq. 1 and the
+radial binning, ending with the binned D(q, tau) copied to the host.
+
+  value     frames/s with the frames already resident in HBM (nfs_push_frames_device)
+  e2e       frames/s through nfs_push_frames from pinned host memory (H2D inside the timed region)
+  roofline  the fused delay kernel: algorithmic bytes per launch / its mean CUDA-event duration
+  plain_f64 the plain unfused FP64 GPU path on the same frames (one pass), and the largest
+            relative difference of its binned D from the fused FP32 path's
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of pairs of the same frames, extrapolated
+            to the whole job by pair count
+
+--impl reference times the FP64 CPU oracle alone (rank 0 only), each step a bounded sample.
+Multi-GPU: each rank analyses its own independent sequence (replicas, weak scaling), no collective
+on the data path; the timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import nfs_synth as S  # noqa: E402
+
+METRIC = "frames/s at 2048²,200 delays (fused FP32 vs plain FP64, err≤2e-5); HBM % of peak"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def delay_block_bytes(delays, N, K, M):
+    """Algorithmic bytes of every fused delay launch of one pass over N frames in blocks of K:
+    each distinct ring slot read once (8 B per mode), each active accumulator read and written once
+    (2 x 8 B per mode).  Returns (total bytes, launches, pairs)."""
+    d = np.asarray(delays, np.int64)
+    total = 0
+    launches = 0
+    pairs = 0
+    for t0 in range(0, N, K):
+        nb = min(K, N - t0)
+        t = np.arange(t0, t0 + nb)
+        act = d[d <= t0 + nb - 1]
+        slots = set(t.tolist())
+        for tau in act:
+            s = t[t >= tau] - tau
+            slots.update(s.tolist())
+            pairs += int(s.size)
+        total += 8 * M * len(slots) + 16 * M * int(act.size)
+        launches += 1
+    return total, launches, pairs
+
+
+def oracle_sample(frames_host, budget_s, cores):
+    """Time the FP64 oracle on the first n frames with every delay 1..n-1; n sized from a one-pair probe."""
+    import oracle
+    oracle.build()
+    H, W = frames_host.shape[1:]
+    t = time.perf_counter()
+    oracle.structure_function(frames_host[:2], [1], 8, nthreads=1)
+    per_pair = time.perf_counter() - t
+    target_pairs = max(3, int(budget_s * cores / max(per_pair, 1e-6)))
+    n = 2
+    while (n + 1) * n // 2 <= target_pairs and n < frames_host.shape[0]:
+        n += 1
+    delays = list(range(1, n))
+    t = time.perf_counter()
+    oracle.structure_function(frames_host[:n], delays, 8, nthreads=cores)
+    dt = time.perf_counter() - t
+    return n, n * (n - 1) // 2, dt
+
+
+def run_reference(args, w):
+    """The FP64 CPU oracle alone, each step a bounded sample; rank 0 prints."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import torch
+    cores = len(os.sched_getaffinity(0))
+    src = S.workload_source(w, device="cpu", dtype=torch.float32)
+    n_s = 12
+    fr = src.frames_numpy(n_s)
+    import oracle
+    oracle.build()
+    pairs_per_step = n_s * (n_s - 1) // 2
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle.structure_function(fr[:3], [1, 2], 8, nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.structure_function(fr, list(range(1, n_s)), 8, nthreads=cores)
+        times.append(time.perf_counter() - t)
+    per_pair = sum(times) / (len(times) * pairs_per_step)
+    value = w.N / (per_pair * w.pair_total)
+    ms = 1000.0 * sum(times) / len(times)
+    sample = (f"{n_s} frames of {w.H}x{w.W}, delays 1..{n_s - 1} ({pairs_per_step} pair FFTs) per step; "
+              f"extrapolated by pair count to the job's {w.pair_total} pairs")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
+                       "n_qbins": w.n_qbins},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS))
+    ap.add_argument("--frames", type=int, default=0, help="override N (smaller runs; not a bench value)")
+    ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    w = S.WORKLOADS[args.workload]
+    if args.frames:
+        import dataclasses
+        w = dataclasses.replace(w, N=args.frames)
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import torch
+    import paper_1209_3362_gb300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    P.build()
+    P.load_library()
+    hbm_peak, peak_src = load_peaks()
+
+    # ---- inputs: the rank's own sequence, generated on its GPU, resident in HBM
+    src = S.OUFrameSource(w.H, w.W, w.Dc, w.gamma0, eps=w.eps, seed=w.seed + 7919 * rank, device="cuda",
+                          dtype=torch.float32)
+    frames = torch.empty((w.N, w.H, w.W), dtype=torch.int16, device="cuda")
+    gb = 16
+    for o in range(0, w.N, gb):
+        n = min(gb, w.N - o)
+        frames[o:o + n] = src.next_frames(n)
+    del src
+    torch.cuda.synchronize()
+
+    ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
+    K = ctx.get_option(P.OPT_BLOCK_FRAMES)
+    pitch = ctx.get_option(P.OPT_PITCH)
+    M = w.H * pitch
+    stream = torch.cuda.ExternalStream(ctx.stream)
+
+    def step():
+        ctx.reset()
+        ctx.push_frames_device(frames)
+        return ctx.structure_function()
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    ctx.set_option(P.OPT_TIMING, 1)
+    ctx.reset_timings()
+    l0 = ctx.launch_count
+    barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launch_count - l0
+    dev_ms = ev0.elapsed_time(ev1)
+    step_ms = max_over_ranks(max(dev_ms, 1000.0 * wall) / args.steps)
+    value = world * w.N / (step_ms / 1000.0)
+    tim = ctx.timings()
+    D32 = res["D"]
+
+    # ---- roofline of the fused delay kernel
+    alg_bytes, n_launch, pairs = delay_block_bytes(w.delays, w.N, K, M)
+    delay_ms, delay_n = tim["delay"]
+    per_launch_ms = delay_ms / max(delay_n, 1)
+    achieved = (alg_bytes / n_launch) / (per_launch_ms / 1000.0) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_delay_f32_block",
+                "peak_source": f"{peak_src} hbm_gbs", "bytes_per_launch": alg_bytes / n_launch,
+                "launch_ms": per_launch_ms}
+    stage_ms = {k: v[0] / args.steps for k, v in tim.items()}
+
+    # ---- end to end from pinned host memory
+    e2e = None
+    if not args.no_e2e:
+        host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
+        host.copy_(frames)
+        del frames
+        torch.cuda.empty_cache()
+        frames = None
+        ctx.set_option(P.OPT_TIMING, 0)
+
+        def step_host():
+            ctx.reset()
+            ctx.push_frames(host)
+            return ctx.structure_function()
+
+        step_host()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_host()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": world * w.N / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
+               "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
+    ctx.close()
+
+    # ---- the plain unfused FP64 GPU path, one pass on the same frames
+    plain = None
+    if not args.no_f64:
+        if frames is None:
+            frames = host.cuda() if e2e is not None else None
+        c64 = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f64")
+        s64 = torch.cuda.ExternalStream(c64.stream)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s64)
+        c64.push_frames_device(frames)
+        r64 = c64.structure_function()
+        e1.record(s64)
+        e1.synchronize()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        m = (r64["bin_counts"][None, :] > 0) & (r64["pair_counts"][:, None] > 0)
+        err = float(np.max(np.abs(D32[m] - r64["D"][m]) / np.abs(r64["D"][m])))
+        plain = {"value": world * w.N / (ms64 / 1000.0), "unit": "frames/s", "ms_per_pass": ms64,
+                 "max_rel_err_f32_vs_f64": err}
+        c64.close()
+
+    # ---- CPU baseline: the FP64 oracle on a bounded sample of the same frames (rank 0)
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        if frames is None:
+            frames = host.cuda()
+        nmax = 40
+        fh = frames[:nmax].cpu().numpy().view(np.uint16)
+        cores = len(os.sched_getaffinity(0))
+        n_s, p_s, dt = oracle_sample(fh, args.cpu_budget, cores)
+        cpu = {"value": w.N / (dt / p_s * w.pair_total), "unit": "frames/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n_s} frames, delays 1..{n_s - 1}: {p_s} pair FFTs of {w.H}x{w.W} in {dt:.1f} s, "
+                         f"extrapolated by pair count to {w.pair_total} pairs"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
+                           "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
+                           "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (frames "
+                           f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "
+                           f"{ctx_bytes(w, K, pitch) / 1e9:.1f} GB per rank)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clk.summary(), "plain_f64_gpu": plain, "stage_ms_per_step": stage_ms,
+                "delay_pairs_per_step": pairs}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def ctx_bytes(w, K, pitch):
+    return (w.delays[-1] + K) * w.H * pitch * 8
+
+
+if __name__ == "__main__":
+    main()

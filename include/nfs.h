@@ -1,0 +1,172 @@
+/*
+ * nfs.h -- C ABI of the GB300 library for the double-frame differential analysis of dynamic
+ * near-field-scattering (shadowgraph, Schlieren, DDM) image sequences, after Cerchiari, Croccolo,
+ * Cardinaux and Scheffold, arXiv:1209.3362.
+ *
+ * The library computes, for a stream of camera frames i_t(x) (uint16, H x W, row-major):
+ *
+ *   n_t(x)        = i_t(x) / <i_t>_x                 (frames normalised by their spatial average)
+ *   Delta I(k, t, tau) = FT[n_t - n_{t+tau}](k)        (spatial Fourier transform of a difference)
+ *   D(k, tau)     = < |Delta I(k, t, tau)|^2 >_t        (left-hand side of Eq. 1, averaged over every
+ *                                                      pair t, t+tau of a stationary sequence)
+ *   D_b(tau)      = azimuthal average of D(k, tau) over the radial bin b   (Fig. 1e,f)
+ *
+ * The Fourier transform is the unscaled forward DFT, exp(-2 pi i (k_x x / W + k_y y / H)).  By
+ * linearity (processing paragraph of the paper) each frame is transformed once and pairs differ
+ * in Fourier space.  Radial bins: with |f| the mode frequency in cycles/px, bin b holds the modes
+ * with b <= 2 n_q |f| < b + 1 (integer-exact rule: L = lcm(H, W), m = k_x L / W, n = k_y' L / H with
+ * k_y' the signed row frequency, bin = floor(isqrt(4 n_q^2 (m^2 + n^2)) / L)); the DC mode and
+ * |f| >= 0.5 are left out; half-plane modes count twice except on the k_x = 0 and k_x = W/2
+ * columns, so bin sums equal full-plane sums.  q = 2 pi |f| rad/px.
+ *
+ * Conventions for every call:
+ *   - Return value: NFS_OK (0) or a negative status below.  nfs_strerror() names it; the context
+ *     keeps the text of its last CUDA error (nfs_last_error()).
+ *   - A CUDA error inside asynchronous work is sticky: every later call on that context returns
+ *     NFS_ECUDA until nfs_destroy().
+ *   - All device memory and streams belong to the context.  Host pointers passed in are only
+ *     read or written during the call.
+ *   - A context is used by one host thread at a time; contexts are independent of each other.
+ *   - The device current at nfs_create() is the context's device; every call makes it current.
+ */
+#ifndef NFS_H
+#define NFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NFS_OK 0
+#define NFS_EINVAL (-1)       /* bad argument (NULL pointer, non-increasing delays, n < 0, ...) */
+#define NFS_EUNSUPPORTED (-2) /* frame shape outside what the kernels handle */
+#define NFS_ENOMEM (-3)       /* device or pinned host allocation failed */
+#define NFS_ECUDA (-4)        /* a CUDA call or kernel failed (sticky) */
+#define NFS_ESTATE (-5)       /* call not allowed in the context's current state */
+
+/* Arithmetic of the analysis path. */
+#define NFS_PATH_FUSED_F32 0 /* FP32 frames and spectra, blocked fused delay update, Kahan-FP32
+                                accumulators, FP64 mean and bin sums (the fast path) */
+#define NFS_PATH_PLAIN_F64 1 /* FP64 everywhere, one frame per delay update, unfused (comparator) */
+
+typedef struct nfs_ctx nfs_ctx;
+
+/*
+ * Create an analysis context (Eq. 1 for a single image sequence).
+ *   H, W      frame height and width in pixels: even, 2 <= H, W <= 4096, prime factors 2 and 3
+ *             only; otherwise NFS_EUNSUPPORTED.
+ *   delays    n_delays frame delays tau_j, strictly increasing, tau_0 >= 0 (tau = 0 is allowed and
+ *             gives D = 0 exactly), tau_max <= 65536.  Copied by the call.
+ *   n_qbins   number of radial bins, 1..65536; bins span 0 <= |f| < 0.5 cycles/px evenly.
+ *   *out      receives the context; NULL on failure.
+ * Allocates the spectrum ring (tau_max + K slots of H x (W/2+1) complex values), the
+ * accumulators (n_delays x H x (W/2+1)) and the staging buffers on the current device.
+ * Uses NFS_PATH_FUSED_F32.
+ */
+int nfs_create(int H, int W, const int32_t *delays, int n_delays, int n_qbins, nfs_ctx **out);
+
+/*
+ * Same as nfs_create with an explicit path (NFS_PATH_*) and block size K (frames per fused delay
+ * update; 0 = library default).  The plain FP64 path ignores K (it updates once per frame).
+ */
+int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block_frames,
+                  nfs_ctx **out);
+
+/*
+ * Append n_frames frames from HOST memory, contiguous [n_frames][H][W] uint16, row-major.
+ * Counts above 4095 are allowed (no clipping).  The frames are copied to the device before the
+ * call returns, so the caller may reuse the buffer at once; the analysis itself runs
+ * asynchronously on the context's stream.  Page-locked buffers are copied by DMA directly;
+ * pageable ones pass through the context's pinned staging buffers.
+ * A frame whose pixels sum to 0 has no mean: its normalised image is taken as 0.
+ * Returns the status of earlier asynchronous work as well (sticky error).
+ */
+int nfs_push_frames(nfs_ctx *ctx, const uint16_t *host_frames, int n_frames);
+
+/*
+ * Append n_frames frames already in DEVICE memory of the context's device (same layout as
+ * nfs_push_frames).  The buffer must stay valid and unchanged until the context's stream has
+ * passed the work (nfs_synchronize() or any call that returns results).  The address must be
+ * 2-byte aligned; 16-byte alignment with W a multiple of 8 takes the vectorised loads.
+ */
+int nfs_push_frames_device(nfs_ctx *ctx, const uint16_t *dev_frames, int n_frames);
+
+/*
+ * Finish the frames pushed so far (including a partial block) and return the binned structure
+ * function.  Caller-owned host outputs:
+ *   D           [n_delays][n_qbins]  D_b(tau_j) = sum_{k in b} w_k D(k, tau_j) / C_b
+ *   bin_counts  [n_qbins]            C_b (integer mode weights; exact)
+ *   pair_counts [n_delays]           number of frame pairs averaged at tau_j: max(0, N - tau_j)
+ *   q_mean      [n_qbins] or NULL    mean q (rad/px) of the bin
+ * An entry with no pairs or an empty bin is 0 (its count tells it apart).  May be called
+ * repeatedly while frames keep coming (a running result).  Synchronises the stream.
+ */
+int nfs_structure_function(nfs_ctx *ctx, double *D, int64_t *bin_counts, int64_t *pair_counts, double *q_mean);
+
+/*
+ * The 2-D spectrum D(k, tau_j) for one delay index j before binning, as FP64 [H][W/2+1]
+ * (k_x fastest, k_y = 0..H-1 in FFT order).  Flushes pending frames and synchronises.
+ */
+int nfs_export_spectrum(nfs_ctx *ctx, int delay_index, double *out);
+
+/* Forget all frames (accumulators to zero, frame count to 0); keeps allocations and options. */
+int nfs_reset(nfs_ctx *ctx);
+
+/* Wait for all work queued on the context; returns the sticky status. */
+int nfs_synchronize(nfs_ctx *ctx);
+
+/* Frames pushed so far. */
+int64_t nfs_frame_count(const nfs_ctx *ctx);
+
+/* Destroy the context and free everything it owns; NULL is accepted. */
+void nfs_destroy(nfs_ctx *ctx);
+
+/* Static text for a status code. */
+const char *nfs_strerror(int status);
+
+/* Text of the context's last CUDA error ("" if none). */
+const char *nfs_last_error(const nfs_ctx *ctx);
+
+/* The cudaStream_t the context launches on, as void*. */
+void *nfs_get_stream(const nfs_ctx *ctx);
+
+/* Option keys for nfs_set_option / nfs_get_option. */
+#define NFS_OPT_TIMING 1      /* 1 = record CUDA events around every kernel launch (default 0) */
+#define NFS_OPT_BLOCK_FRAMES 2 /* read-only: K */
+#define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K */
+#define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
+#define NFS_OPT_PATH 5         /* read-only: NFS_PATH_* */
+#define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..64; default 4) */
+#define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel variant (0 = default) */
+int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);
+int nfs_get_option(const nfs_ctx *ctx, int key, int64_t *value);
+
+/* Stages reported by nfs_get_timings. */
+#define NFS_STAGE_H2D 0   /* host-to-device frame copies */
+#define NFS_STAGE_MEAN 1  /* per-frame exact integer sums (spatial mean) */
+#define NFS_STAGE_ROWFFT 2 /* normalisation + row r2c FFTs */
+#define NFS_STAGE_COLFFT 3 /* column FFTs into the spectrum ring */
+#define NFS_STAGE_DELAY 4 /* delay update of the accumulators */
+#define NFS_STAGE_BIN 5   /* radial binning */
+#define NFS_N_STAGES 6
+
+/*
+ * Per-stage totals since the last nfs_reset_timings(): ms[s] = summed device time of the launches
+ * of stage s (CUDA events on the context's stream), launches[s] = their number.  Needs
+ * NFS_OPT_TIMING = 1; synchronises.  Arrays have NFS_N_STAGES entries.
+ */
+int nfs_get_timings(nfs_ctx *ctx, double *ms, int64_t *launches);
+int nfs_reset_timings(nfs_ctx *ctx);
+
+/*
+ * Number of kernel launches the context has issued since creation (all stages, both paths).
+ */
+int64_t nfs_launch_count(const nfs_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NFS_H */

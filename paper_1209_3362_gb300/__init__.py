@@ -1,0 +1,229 @@
+"""Python binding of the GB300 NFS structure-function library (include/nfs.h).
+
+Argument marshalling only: every step of the analysis (mean normalisation, FFTs, the delay update
+of Eq. 1, radial binning) runs in the library's CUDA kernels.  There is no CPU fallback: if the
+library is missing, importing works but constructing ``NFS`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+LIB_PATH = os.path.join(HERE, "_build", "libnfs_gb300.so")
+HEADER = os.path.join(ROOT, "include", "nfs.h")
+
+NFS_OK = 0
+NFS_EINVAL = -1
+NFS_EUNSUPPORTED = -2
+NFS_ENOMEM = -3
+NFS_ECUDA = -4
+NFS_ESTATE = -5
+PATH_FUSED_F32 = 0
+PATH_PLAIN_F64 = 1
+OPT_TIMING = 1
+OPT_BLOCK_FRAMES = 2
+OPT_RING_SLOTS = 3
+OPT_PITCH = 4
+OPT_PATH = 5
+OPT_FFT_CHUNK = 6
+OPT_DELAY_VARIANT = 7
+STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
+
+_lib = None
+
+
+class NFSError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_text(status)} ({status}){': ' + detail if detail else ''}")
+
+
+def build(force: bool = False) -> str:
+    from . import buildlib as _b
+    return _b.build(force=force)
+
+
+def load_library(path: Optional[str] = None):
+    """Load libnfs_gb300.so and declare its signatures (raises if it was not built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing (run __graft_entry__.build())")
+    L = ctypes.CDLL(p)
+    V, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    sig = {
+        "nfs_create": (I, [I, I, V, I, I, PP]),
+        "nfs_create_ex": (I, [I, I, V, I, I, I, I, PP]),
+        "nfs_push_frames": (I, [V, V, I]),
+        "nfs_push_frames_device": (I, [V, V, I]),
+        "nfs_structure_function": (I, [V, V, V, V, V]),
+        "nfs_export_spectrum": (I, [V, I, V]),
+        "nfs_reset": (I, [V]),
+        "nfs_synchronize": (I, [V]),
+        "nfs_frame_count": (I64, [V]),
+        "nfs_destroy": (None, [V]),
+        "nfs_strerror": (ctypes.c_char_p, [I]),
+        "nfs_last_error": (ctypes.c_char_p, [V]),
+        "nfs_get_stream": (V, [V]),
+        "nfs_set_option": (I, [V, I, I64]),
+        "nfs_get_option": (I, [V, I, ctypes.POINTER(I64)]),
+        "nfs_get_timings": (I, [V, V, V]),
+        "nfs_reset_timings": (I, [V]),
+        "nfs_launch_count": (I64, [V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    if path is None:
+        _lib = L
+    return L
+
+
+def header_functions(header: str = HEADER):
+    """Names of the functions declared in the public header."""
+    text = open(header).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(nfs_[a-z0-9_]+)\s*\(", text)))
+
+
+def status_text(status: int) -> str:
+    try:
+        return load_library().nfs_strerror(status).decode()
+    except Exception:
+        return {0: "ok", -1: "invalid argument", -2: "unsupported frame shape", -3: "out of memory",
+                -4: "CUDA error", -5: "call not allowed in this state"}.get(status, "unknown status")
+
+
+def _ptr(a):
+    return ctypes.c_void_p(a.ctypes.data) if a is not None else None
+
+
+class NFS:
+    """One analysis context: frames in, binned structure function D_b(tau) out (Eq. 1, Fig. 1e,f)."""
+
+    def __init__(self, H: int, W: int, delays: Sequence[int], n_qbins: int, path: str = "f32",
+                 block_frames: int = 0):
+        self._L = load_library()
+        self.H, self.W = int(H), int(W)
+        self.delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+        self.n_qbins = int(n_qbins)
+        self.path = {"f32": PATH_FUSED_F32, "f64": PATH_PLAIN_F64}[path]
+        h = ctypes.c_void_p()
+        rc = self._L.nfs_create_ex(self.H, self.W, _ptr(self.delays), int(self.delays.size), self.n_qbins,
+                                   self.path, int(block_frames), ctypes.byref(h))
+        if rc != NFS_OK:
+            raise NFSError(rc, "nfs_create_ex")
+        self._h = h
+
+    # --------------------------------------------------------------- helpers
+    def _check(self, rc: int, what: str):
+        if rc != NFS_OK:
+            detail = self._L.nfs_last_error(self._h) if self._h else b""
+            raise NFSError(rc, what, (detail or b"").decode())
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.nfs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # --------------------------------------------------------------- frames
+    def push_frames(self, frames) -> None:
+        """Host frames [n, H, W] uint16 (numpy, or a CPU torch tensor, pinned or not)."""
+        if hasattr(frames, "data_ptr"):
+            t = frames
+            assert not t.is_cuda and t.is_contiguous() and t.element_size() == 2
+            n = t.shape[0] if t.dim() == 3 else 1
+            self._check(self._L.nfs_push_frames(self._h, ctypes.c_void_p(t.data_ptr()), n), "nfs_push_frames")
+            return
+        a = np.ascontiguousarray(frames, dtype=np.uint16)
+        if a.ndim == 2:
+            a = a[None]
+        assert a.shape[1:] == (self.H, self.W), a.shape
+        self._check(self._L.nfs_push_frames(self._h, _ptr(a), a.shape[0]), "nfs_push_frames")
+
+    def push_frames_device(self, frames) -> None:
+        """Device frames: a CUDA torch tensor [n, H, W] of 2-byte integers (int16 storage of counts)."""
+        assert frames.is_cuda and frames.is_contiguous() and frames.element_size() == 2
+        n = frames.shape[0] if frames.dim() == 3 else 1
+        self._check(self._L.nfs_push_frames_device(self._h, ctypes.c_void_p(frames.data_ptr()), n),
+                    "nfs_push_frames_device")
+
+    def push_frames_device_ptr(self, ptr: int, n: int) -> None:
+        self._check(self._L.nfs_push_frames_device(self._h, ctypes.c_void_p(ptr), int(n)), "nfs_push_frames_device")
+
+    # --------------------------------------------------------------- results
+    def structure_function(self) -> dict:
+        nd, nq = self.delays.size, self.n_qbins
+        D = np.zeros((nd, nq), np.float64)
+        bc = np.zeros(nq, np.int64)
+        pc = np.zeros(nd, np.int64)
+        qm = np.zeros(nq, np.float64)
+        self._check(self._L.nfs_structure_function(self._h, _ptr(D), _ptr(bc), _ptr(pc), _ptr(qm)),
+                    "nfs_structure_function")
+        return dict(D=D, bin_counts=bc, pair_counts=pc, q_mean=qm)
+
+    def export_spectrum(self, j: int) -> np.ndarray:
+        out = np.zeros((self.H, self.W // 2 + 1), np.float64)
+        self._check(self._L.nfs_export_spectrum(self._h, int(j), _ptr(out)), "nfs_export_spectrum")
+        return out
+
+    def reset(self):
+        self._check(self._L.nfs_reset(self._h), "nfs_reset")
+
+    def synchronize(self):
+        self._check(self._L.nfs_synchronize(self._h), "nfs_synchronize")
+
+    @property
+    def frame_count(self) -> int:
+        return int(self._L.nfs_frame_count(self._h))
+
+    @property
+    def stream(self) -> int:
+        return int(self._L.nfs_get_stream(self._h) or 0)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._L.nfs_launch_count(self._h))
+
+    def set_option(self, key: int, value: int):
+        self._check(self._L.nfs_set_option(self._h, int(key), int(value)), "nfs_set_option")
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        self._check(self._L.nfs_get_option(self._h, int(key), ctypes.byref(v)), "nfs_get_option")
+        return int(v.value)
+
+    def timings(self) -> dict:
+        ms = np.zeros(len(STAGES), np.float64)
+        n = np.zeros(len(STAGES), np.int64)
+        self._check(self._L.nfs_get_timings(self._h, _ptr(ms), _ptr(n)), "nfs_get_timings")
+        return {s: (float(ms[i]), int(n[i])) for i, s in enumerate(STAGES)}
+
+    def reset_timings(self):
+        self._check(self._L.nfs_reset_timings(self._h), "nfs_reset_timings")

@@ -1,0 +1,74 @@
+// Ingest kernels: the exact spatial sum of every frame (for the mean normalisation of the
+// differential analysis: images are divided by their spatial average) and the FP32 reference
+// image subtracted before the FP32 transform.
+#include "nfs_internal.cuh"
+
+namespace nfs {
+
+// sums[blockIdx.y] += sum of the frame's pixels.  Integer arithmetic, so the result is exact and
+// independent of the order of the atomic adds.  VEC: 16-byte loads (frame start 16-byte aligned).
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_frame_sums(const uint16_t *__restrict__ frames, size_t HW,
+                                                    unsigned long long *__restrict__ sums)
+{
+    const uint16_t *f = frames + (size_t)blockIdx.y * HW;
+    unsigned long long acc = 0;
+    size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t nthr = (size_t)gridDim.x * blockDim.x;
+    size_t done = 0;
+    if (VEC) {
+        const uint4 *v = reinterpret_cast<const uint4 *>(f);
+        size_t n8 = HW / 8;
+        for (size_t i = tid; i < n8; i += nthr) {
+            uint4 q = __ldg(v + i);
+            unsigned int s = (q.x & 0xffffu) + (q.x >> 16) + (q.y & 0xffffu) + (q.y >> 16) + (q.z & 0xffffu) +
+                             (q.z >> 16) + (q.w & 0xffffu) + (q.w >> 16);
+            acc += s;
+        }
+        done = n8 * 8;
+    }
+    for (size_t i = done + tid; i < HW; i += nthr) acc += f[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0 && acc) atomicAdd(&sums[blockIdx.y], acc);
+}
+
+cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
+                              cudaStream_t s)
+{
+    if (nf <= 0) return cudaSuccess;
+    bool vec = ((reinterpret_cast<uintptr_t>(frames) & 15) == 0) && ((g.HW * 2) % 16 == 0);
+    size_t work = vec ? g.HW / 8 : g.HW;
+    int bx = (int)((work + 255) / 256);
+    int cap = (nf >= 8) ? 64 : 512 / nf;
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    dim3 grid(bx, nf);
+    if (vec)
+        k_frame_sums<true><<<grid, 256, 0, s>>>(frames, g.HW, sums);
+    else
+        k_frame_sums<false><<<grid, 256, 0, s>>>(frames, g.HW, sums);
+    return cudaGetLastError();
+}
+
+// ref[x] = fl32( i_0(x) * fl32(HW / S_0) ), rounded products without contraction so the row pass
+// reproduces it exactly for frame 0 (its normalised-and-shifted image is then exactly 0).
+__global__ void k_reference(const uint16_t *__restrict__ frame0, const unsigned long long *__restrict__ sum0,
+                            size_t HW, float *__restrict__ ref)
+{
+    unsigned long long S = *sum0;
+    float inv = S ? (float)((double)HW / (double)S) : 0.0f;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += (size_t)gridDim.x * blockDim.x)
+        ref[i] = __fmul_rn((float)frame0[i], inv);
+}
+
+cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
+                             float *ref, cudaStream_t s)
+{
+    int bx = (int)((g.HW + 255) / 256);
+    if (bx > 1216) bx = 1216;
+    k_reference<<<bx, 256, 0, s>>>(frame0, sum0, g.HW, ref);
+    return cudaGetLastError();
+}
+
+}  // namespace nfs

@@ -1,0 +1,697 @@
+// Host side of the C ABI declared in include/nfs.h: context lifecycle, the frame pipeline
+// (copy -> exact mean -> row FFT -> column FFT -> delay update), binning tables and timings.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "nfs_internal.cuh"
+
+using namespace nfs;
+
+namespace {
+
+constexpr int kDefaultBlock = 32;   // K: frames per fused delay update
+constexpr int kMaxBlock = 32;       // largest K the fused kernel takes
+constexpr int kMaxChunk = 64;       // largest FFT chunk
+constexpr int kMaxDim = 4096;
+constexpr int kMaxDelay = 65536;
+
+bool factors_2_3(int n)
+{
+    if (n <= 0) return false;
+    while (n % 2 == 0) n /= 2;
+    while (n % 3 == 0) n /= 3;
+    return n == 1;
+}
+
+long long gcd_ll(long long a, long long b)
+{
+    while (b) {
+        long long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+unsigned long long isqrt_ull(unsigned long long v)
+{
+    unsigned long long r = (unsigned long long)std::sqrt((double)v);
+    while (r > 0 && r * r > v) --r;
+    while ((r + 1) * (r + 1) <= v) ++r;
+    return r;
+}
+
+struct TimedPair {
+    int stage;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct nfs_ctx {
+    Geometry g{};
+    int path = NFS_PATH_FUSED_F32;
+    int K = kDefaultBlock;
+    int R = 0, nd = 0, nq = 0;
+    int fft_chunk = 4;
+    int stage_frames = 1;
+    int delay_variant = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    std::vector<int32_t> delays;
+    int tau_max = 0;
+
+    uint16_t *d_stage[2] = {nullptr, nullptr};
+    uint16_t *h_stage[2] = {nullptr, nullptr};
+    cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
+    int stage_i = 0;
+
+    unsigned long long *d_sums = nullptr;
+    float *d_ref = nullptr;
+    void *d_ring = nullptr;
+    void *d_acc = nullptr;
+    int *d_delays = nullptr;
+    void *d_tw_row = nullptr, *d_tw_post = nullptr, *d_tw_col = nullptr;
+    FftPlan plan_row, plan_col;
+    int *d_bin_off = nullptr, *d_bin_modes = nullptr;
+    long long *d_pairs = nullptr, *d_counts = nullptr;
+    double *d_D = nullptr, *d_export = nullptr;
+
+    std::vector<long long> counts, pairs_h;
+    std::vector<double> qmean;
+    long long nframes = 0, nprocessed = 0;
+    bool have_ref = false;
+
+    int err = NFS_OK;
+    std::string errmsg;
+
+    bool timing = false;
+    std::vector<TimedPair> pending;
+    std::vector<cudaEvent_t> pool;
+    double stage_ms[NFS_N_STAGES] = {};
+    long long stage_n[NFS_N_STAGES] = {};
+    long long launches = 0;
+
+    bool f32() const { return path == NFS_PATH_FUSED_F32; }
+    size_t csize() const { return f32() ? sizeof(float2) : sizeof(double2); }
+    size_t asize() const { return f32() ? sizeof(float2) : sizeof(double); }
+    size_t frame_bytes() const { return g.HW * sizeof(uint16_t); }
+};
+
+namespace {
+
+int set_cuda_error(nfs_ctx *c, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return NFS_OK;
+    char buf[256];
+    snprintf(buf, sizeof(buf), "%s: %s", where, cudaGetErrorString(e));
+    c->errmsg = buf;
+    if (c->err == NFS_OK) c->err = NFS_ECUDA;
+    return NFS_ECUDA;
+}
+
+#define CK(ctx, call)                                                   \
+    do {                                                                \
+        cudaError_t _e = (call);                                        \
+        if (_e != cudaSuccess) return set_cuda_error((ctx), _e, #call); \
+    } while (0)
+
+cudaEvent_t pool_get(nfs_ctx *c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Runs one launcher with optional event timing around it.
+template <class F>
+int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (c->timing) {
+        a = pool_get(c);
+        b = pool_get(c);
+        if (!a || !b) return set_cuda_error(c, cudaErrorMemoryAllocation, "cudaEventCreate");
+        CK(c, cudaEventRecord(a, s));
+    }
+    cudaError_t e = f();
+    if (e != cudaSuccess) return set_cuda_error(c, e, what);
+    if (c->timing) {
+        CK(c, cudaEventRecord(b, s));
+        c->pending.push_back({stage, a, b});
+    }
+    if (stage != NFS_STAGE_H2D) c->launches++;
+    return NFS_OK;
+}
+
+int harvest(nfs_ctx *c)
+{
+    for (auto &p : c->pending) {
+        float ms = 0.f;
+        CK(c, cudaEventSynchronize(p.b));
+        CK(c, cudaEventElapsedTime(&ms, p.a, p.b));
+        c->stage_ms[p.stage] += ms;
+        c->stage_n[p.stage] += 1;
+        c->pool.push_back(p.a);
+        c->pool.push_back(p.b);
+    }
+    c->pending.clear();
+    return NFS_OK;
+}
+
+template <typename T>
+int upload_twiddles(nfs_ctx *c, int L, void **dst)
+{
+    using C = typename cplx_t<T>::type;
+    std::vector<C> h((size_t)std::max(L, 1));
+    for (int m = 0; m < L; ++m) {
+        double a = 2.0 * M_PI * (double)m / (double)L;
+        h[m].x = (T)std::cos(a);
+        h[m].y = (T)(-std::sin(a));
+    }
+    CK(c, cudaMalloc(dst, sizeof(C) * h.size()));
+    CK(c, cudaMemcpy(*dst, h.data(), sizeof(C) * h.size(), cudaMemcpyHostToDevice));
+    return NFS_OK;
+}
+
+// r2c post-processing twiddles exp(-2 pi i k / W), k = 0..W/2.
+template <typename T>
+int upload_post(nfs_ctx *c, int W, void **dst)
+{
+    using C = typename cplx_t<T>::type;
+    std::vector<C> h((size_t)(W / 2 + 1));
+    for (int k = 0; k <= W / 2; ++k) {
+        double a = 2.0 * M_PI * (double)k / (double)W;
+        h[k].x = (T)std::cos(a);
+        h[k].y = (T)(-std::sin(a));
+    }
+    CK(c, cudaMalloc(dst, sizeof(C) * h.size()));
+    CK(c, cudaMemcpy(*dst, h.data(), sizeof(C) * h.size(), cudaMemcpyHostToDevice));
+    return NFS_OK;
+}
+
+// Radial bin of every half-plane mode (integer rule of the header), as a CSR list by bin.
+int build_bins(nfs_ctx *c)
+{
+    const int H = c->g.H, W = c->g.W, Wh = c->g.Wh, nq = c->nq;
+    const long long L = (long long)H / gcd_ll(H, W) * W;
+    std::vector<std::vector<int>> lists((size_t)nq);
+    std::vector<double> qsum((size_t)nq, 0.0);
+    c->counts.assign((size_t)nq, 0);
+    for (int ky = 0; ky < H; ++ky) {
+        const long long kys = (ky <= H / 2) ? ky : ky - H;
+        for (int kx = 0; kx < Wh; ++kx) {
+            if (kx == 0 && ky == 0) continue;
+            const long long m = (long long)kx * (L / W), n = kys * (L / H);
+            const unsigned long long r2 = (unsigned long long)(m * m + n * n);
+            const unsigned long long b = isqrt_ull(4ull * (unsigned long long)nq * (unsigned long long)nq * r2) /
+                                         (unsigned long long)L;
+            if (b >= (unsigned long long)nq) continue;
+            const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
+            const long long idx = (long long)ky * c->g.Wp + kx;
+            lists[b].push_back((int)((idx << 1) | two));
+            c->counts[b] += two ? 2 : 1;
+            qsum[b] += (two ? 2.0 : 1.0) * 2.0 * M_PI * std::sqrt((double)r2) / (double)L;
+        }
+    }
+    c->qmean.assign((size_t)nq, 0.0);
+    std::vector<int> off((size_t)nq + 1, 0), modes;
+    for (int b = 0; b < nq; ++b) {
+        off[b + 1] = off[b] + (int)lists[b].size();
+        if (c->counts[b]) c->qmean[b] = qsum[b] / (double)c->counts[b];
+    }
+    modes.reserve((size_t)off[nq]);
+    for (int b = 0; b < nq; ++b) modes.insert(modes.end(), lists[b].begin(), lists[b].end());
+    CK(c, cudaMalloc(&c->d_bin_off, sizeof(int) * off.size()));
+    CK(c, cudaMemcpy(c->d_bin_off, off.data(), sizeof(int) * off.size(), cudaMemcpyHostToDevice));
+    CK(c, cudaMalloc(&c->d_bin_modes, sizeof(int) * std::max<size_t>(modes.size(), 1)));
+    if (!modes.empty())
+        CK(c, cudaMemcpy(c->d_bin_modes, modes.data(), sizeof(int) * modes.size(), cudaMemcpyHostToDevice));
+    CK(c, cudaMalloc(&c->d_counts, sizeof(long long) * (size_t)nq));
+    CK(c, cudaMemcpy(c->d_counts, c->counts.data(), sizeof(long long) * (size_t)nq, cudaMemcpyHostToDevice));
+    return NFS_OK;
+}
+
+void free_all(nfs_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+    for (auto &p : c->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : c->pool) cudaEventDestroy(e);
+    for (int i = 0; i < 2; ++i) {
+        cudaFree(c->d_stage[i]);
+        if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
+        if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
+        if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
+        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+    }
+    cudaFree(c->d_sums);
+    cudaFree(c->d_ref);
+    cudaFree(c->d_ring);
+    cudaFree(c->d_acc);
+    cudaFree(c->d_delays);
+    cudaFree(c->d_tw_row);
+    cudaFree(c->d_tw_post);
+    cudaFree(c->d_tw_col);
+    cudaFree(c->d_bin_off);
+    cudaFree(c->d_bin_modes);
+    cudaFree(c->d_pairs);
+    cudaFree(c->d_counts);
+    cudaFree(c->d_D);
+    cudaFree(c->d_export);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+}
+
+int alloc_dev(nfs_ctx *c, void **p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        *p = nullptr;
+        return NFS_ENOMEM;
+    }
+    return set_cuda_error(c, e, "cudaMalloc");
+}
+
+int flush_block(nfs_ctx *c)
+{
+    const long long nb = c->nframes - c->nprocessed;
+    if (nb <= 0 || !c->f32()) return NFS_OK;
+    DelayArgs a;
+    a.ring = (const float2 *)c->d_ring;
+    a.R = c->R;
+    a.M = c->g.M;
+    a.t0 = c->nprocessed;
+    a.nb = (int)nb;
+    a.delays = c->d_delays;
+    a.nd = c->nd;
+    a.acc = (float2 *)c->d_acc;
+    int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
+                   "delay_f32");
+    if (rc) return rc;
+    c->nprocessed = c->nframes;
+    return NFS_OK;
+}
+
+// Transform nf device-resident frames (nf <= fft chunk) and, when a block is complete, update.
+int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
+{
+    CK(c, cudaMemsetAsync(c->d_sums, 0, sizeof(unsigned long long) * (size_t)nf, c->stream));
+    int rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_frame_sums(dsrc, nf, c->g, c->d_sums, c->stream); },
+                   "frame_sums");
+    if (rc) return rc;
+    if (!c->have_ref && c->f32()) {
+        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, c->d_sums, c->g, c->d_ref, c->stream); },
+                   "reference");
+        if (rc) return rc;
+        c->have_ref = true;
+    }
+    const int slot0 = (int)(c->nframes % c->R);
+    if (c->f32()) {
+        rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
+            return launch_row_fft<float>(dsrc, nf, c->d_sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
+                                         (const float2 *)c->d_tw_post, (float2 *)c->d_ring, c->R, slot0, c->stream);
+        }, "row_fft_f32");
+        if (rc) return rc;
+        rc = timed(c, NFS_STAGE_COLFFT, c->stream, [&] {
+            return launch_col_fft<float>(nf, c->g, c->plan_col, (const float2 *)c->d_tw_col, (float2 *)c->d_ring, c->R,
+                                         slot0, c->stream);
+        }, "col_fft_f32");
+        if (rc) return rc;
+        c->nframes += nf;
+        if (c->nframes - c->nprocessed >= c->K) return flush_block(c);
+        return NFS_OK;
+    }
+    rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
+        return launch_row_fft<double>(dsrc, nf, c->d_sums, nullptr, c->g, c->plan_row, (const double2 *)c->d_tw_row,
+                                      (const double2 *)c->d_tw_post, (double2 *)c->d_ring, c->R, slot0, c->stream);
+    }, "row_fft_f64");
+    if (rc) return rc;
+    rc = timed(c, NFS_STAGE_COLFFT, c->stream, [&] {
+        return launch_col_fft<double>(nf, c->g, c->plan_col, (const double2 *)c->d_tw_col, (double2 *)c->d_ring, c->R,
+                                      slot0, c->stream);
+    }, "col_fft_f64");
+    if (rc) return rc;
+    for (int f = 0; f < nf; ++f) {
+        const long long t = c->nframes + f;
+        rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] {
+            return launch_delay_f64((const double2 *)c->d_ring, c->R, c->g.M, t, c->d_delays, c->nd, (double *)c->d_acc,
+                                    c->stream);
+        }, "delay_f64");
+        if (rc) return rc;
+    }
+    c->nframes += nf;
+    c->nprocessed = c->nframes;
+    if (c->timing && c->pending.size() > 200000) return harvest(c);
+    return NFS_OK;
+}
+
+// Frames the next chunk may take so that a chunk never spans two delay blocks.
+int next_chunk(const nfs_ctx *c, long long remaining, int cap)
+{
+    long long nf = std::min<long long>(remaining, cap);
+    if (c->f32()) nf = std::min<long long>(nf, c->K - (c->nframes - c->nprocessed));
+    return (int)std::max<long long>(nf, 1);
+}
+
+int enter(nfs_ctx *c)
+{
+    if (!c) return NFS_EINVAL;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return set_cuda_error(c, e, "cudaSetDevice");
+    return c->err;
+}
+
+int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out)
+{
+    if (!out) return NFS_EINVAL;
+    *out = nullptr;
+    if (!delays || n_delays <= 0 || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
+    if (path != NFS_PATH_FUSED_F32 && path != NFS_PATH_PLAIN_F64) return NFS_EINVAL;
+    if (block < 0 || block > kMaxBlock) return NFS_EINVAL;
+    for (int j = 0; j < n_delays; ++j) {
+        if (delays[j] < 0 || delays[j] > kMaxDelay) return NFS_EINVAL;
+        if (j && delays[j] <= delays[j - 1]) return NFS_EINVAL;
+    }
+    if (H < 2 || W < 2 || H > kMaxDim || W > kMaxDim || (H % 2) || (W % 2) || !factors_2_3(H) || !factors_2_3(W / 2))
+        return NFS_EUNSUPPORTED;
+
+    nfs_ctx *c = new (std::nothrow) nfs_ctx();
+    if (!c) return NFS_ENOMEM;
+    cudaGetDevice(&c->device);
+    c->path = path;
+    c->K = block ? block : kDefaultBlock;
+    c->nd = n_delays;
+    c->nq = n_qbins;
+    c->delays.assign(delays, delays + n_delays);
+    c->tau_max = delays[n_delays - 1];
+    c->g.H = H;
+    c->g.W = W;
+    c->g.Lr = W / 2;
+    c->g.Wh = W / 2 + 1;
+    c->g.Wp = (c->g.Wh + 3) / 4 * 4;
+    c->g.M = (size_t)H * c->g.Wp;
+    c->g.HW = (size_t)H * W;
+    c->R = c->tau_max + (c->f32() ? c->K : kMaxChunk);
+    c->stage_frames = (int)std::max<size_t>(1, std::min<size_t>(kMaxChunk, (64u << 20) / c->frame_bytes()));
+    c->fft_chunk = std::min(4, c->stage_frames);
+    c->pairs_h.assign((size_t)n_delays, 0);
+
+    int rc = NFS_OK;
+    auto bail = [&](int r) {
+        free_all(c);
+        delete c;
+        return r;
+    };
+    if (!make_plan(c->g.Lr, &c->plan_row) || !make_plan(H, &c->plan_col)) return bail(NFS_EUNSUPPORTED);
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(NFS_ECUDA);
+    for (int i = 0; i < 2; ++i) {
+        if (cudaEventCreateWithFlags(&c->ev_filled[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(NFS_ECUDA);
+        if ((rc = alloc_dev(c, (void **)&c->d_stage[i], c->frame_bytes() * (size_t)c->stage_frames))) return bail(rc);
+    }
+    const size_t ring_bytes = (size_t)c->R * c->g.M * c->csize();
+    const size_t acc_bytes = (size_t)c->nd * c->g.M * c->asize();
+    if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * kMaxChunk))) return bail(rc);
+    if (c->f32() && (rc = alloc_dev(c, (void **)&c->d_ref, sizeof(float) * c->g.HW))) return bail(rc);
+    if ((rc = alloc_dev(c, &c->d_ring, ring_bytes))) return bail(rc);
+    if ((rc = alloc_dev(c, &c->d_acc, acc_bytes))) return bail(rc);
+    if ((rc = alloc_dev(c, (void **)&c->d_delays, sizeof(int) * (size_t)c->nd))) return bail(rc);
+    if ((rc = alloc_dev(c, (void **)&c->d_pairs, sizeof(long long) * (size_t)c->nd))) return bail(rc);
+    if ((rc = alloc_dev(c, (void **)&c->d_D, sizeof(double) * (size_t)c->nd * c->nq))) return bail(rc);
+    if (cudaMemcpy(c->d_delays, c->delays.data(), sizeof(int) * (size_t)c->nd, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(NFS_ECUDA);
+    if (cudaMemset(c->d_acc, 0, acc_bytes) != cudaSuccess) return bail(NFS_ECUDA);
+    if (c->f32()) {
+        if (upload_twiddles<float>(c, c->g.Lr, &c->d_tw_row) || upload_twiddles<float>(c, H, &c->d_tw_col) ||
+            upload_post<float>(c, W, &c->d_tw_post))
+            return bail(NFS_ECUDA);
+    } else {
+        if (upload_twiddles<double>(c, c->g.Lr, &c->d_tw_row) || upload_twiddles<double>(c, H, &c->d_tw_col) ||
+            upload_post<double>(c, W, &c->d_tw_post))
+            return bail(NFS_ECUDA);
+    }
+    if (build_bins(c)) return bail(NFS_ECUDA);
+    *out = c;
+    return NFS_OK;
+}
+
+bool is_page_locked(const void *p)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfs_create(int H, int W, const int32_t *delays, int n_delays, int n_qbins, nfs_ctx **out)
+{
+    return create_impl(H, W, delays, n_delays, n_qbins, NFS_PATH_FUSED_F32, 0, out);
+}
+
+int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block_frames,
+                  nfs_ctx **out)
+{
+    return create_impl(H, W, delays, n_delays, n_qbins, path, block_frames, out);
+}
+
+int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !h)) return NFS_EINVAL;
+    if (n == 0) return NFS_OK;
+    const bool locked = is_page_locked(h);
+    if (!locked && !c->h_stage[0]) {
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaMallocHost((void **)&c->h_stage[i], c->frame_bytes() * (size_t)c->stage_frames);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return NFS_ENOMEM;
+            }
+        }
+    }
+    const int cap = std::min(c->fft_chunk, c->stage_frames);
+    long long done = 0;
+    int last = -1;
+    while (done < n) {
+        const int nf = next_chunk(c, n - done, cap);
+        const int i = c->stage_i;
+        c->stage_i ^= 1;
+        const size_t bytes = c->frame_bytes() * (size_t)nf;
+        const uint16_t *src = h + (size_t)done * c->g.HW;
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[i], 0));
+        if (!locked) {
+            CK(c, cudaEventSynchronize(c->ev_copied[i]));
+            memcpy(c->h_stage[i], src, bytes);
+            src = c->h_stage[i];
+        }
+        rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
+            return cudaMemcpyAsync(c->d_stage[i], src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
+        }, "h2d");
+        if (rc) return rc;
+        CK(c, cudaEventRecord(c->ev_copied[i], c->copy_stream));
+        CK(c, cudaEventRecord(c->ev_filled[i], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[i], 0));
+        rc = process_chunk(c, c->d_stage[i], nf);
+        if (rc) return rc;
+        CK(c, cudaEventRecord(c->ev_free[i], c->stream));
+        done += nf;
+        last = i;
+    }
+    if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_copied[last]));
+    return c->err;
+}
+
+int nfs_push_frames_device(nfs_ctx *c, const uint16_t *d, int n)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 1)) return NFS_EINVAL;
+    long long done = 0;
+    while (done < n) {
+        const int nf = next_chunk(c, n - done, c->fft_chunk);
+        rc = process_chunk(c, d + (size_t)done * c->g.HW, nf);
+        if (rc) return rc;
+        done += nf;
+    }
+    return c->err;
+}
+
+int nfs_structure_function(nfs_ctx *c, double *D, int64_t *bin_counts, int64_t *pair_counts, double *q_mean)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!D || !bin_counts || !pair_counts) return NFS_EINVAL;
+    if ((rc = flush_block(c))) return rc;
+    for (int j = 0; j < c->nd; ++j) c->pairs_h[j] = std::max<long long>(0, c->nframes - c->delays[j]);
+    CK(c, cudaMemcpyAsync(c->d_pairs, c->pairs_h.data(), sizeof(long long) * (size_t)c->nd, cudaMemcpyHostToDevice,
+                          c->stream));
+    rc = timed(c, NFS_STAGE_BIN, c->stream, [&] {
+        return c->f32() ? launch_bin<float2>((const float2 *)c->d_acc, c->g.M, c->nd, c->nq, c->d_bin_off,
+                                             c->d_bin_modes, c->d_pairs, c->d_counts, c->d_D, c->stream)
+                        : launch_bin<double>((const double *)c->d_acc, c->g.M, c->nd, c->nq, c->d_bin_off,
+                                             c->d_bin_modes, c->d_pairs, c->d_counts, c->d_D, c->stream);
+    }, "bin");
+    if (rc) return rc;
+    CK(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * (size_t)c->nd * c->nq, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < c->nq; ++b) bin_counts[b] = c->counts[b];
+    for (int j = 0; j < c->nd; ++j) pair_counts[j] = c->pairs_h[j];
+    if (q_mean)
+        for (int b = 0; b < c->nq; ++b) q_mean[b] = c->qmean[b];
+    if (c->timing && (rc = harvest(c))) return rc;
+    return c->err;
+}
+
+int nfs_export_spectrum(nfs_ctx *c, int j, double *out)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!out || j < 0 || j >= c->nd) return NFS_EINVAL;
+    if ((rc = flush_block(c))) return rc;
+    const size_t n = (size_t)c->g.H * c->g.Wh;
+    if (!c->d_export && (rc = alloc_dev(c, (void **)&c->d_export, sizeof(double) * n))) return rc;
+    const long long pairs = std::max<long long>(0, c->nframes - c->delays[j]);
+    cudaError_t e = c->f32() ? launch_export<float2>((const float2 *)c->d_acc + (size_t)j * c->g.M, c->g, pairs,
+                                                     c->d_export, c->stream)
+                             : launch_export<double>((const double *)c->d_acc + (size_t)j * c->g.M, c->g, pairs,
+                                                     c->d_export, c->stream);
+    CK(c, e);
+    c->launches++;
+    CK(c, cudaMemcpyAsync(out, c->d_export, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return c->err;
+}
+
+int nfs_reset(nfs_ctx *c)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    CK(c, cudaMemsetAsync(c->d_acc, 0, (size_t)c->nd * c->g.M * c->asize(), c->stream));
+    c->nframes = 0;
+    c->nprocessed = 0;
+    c->have_ref = false;
+    return NFS_OK;
+}
+
+int nfs_synchronize(nfs_ctx *c)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    CK(c, cudaStreamSynchronize(c->copy_stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (c->timing && (rc = harvest(c))) return rc;
+    return c->err;
+}
+
+int64_t nfs_frame_count(const nfs_ctx *c) { return c ? c->nframes : -1; }
+
+void nfs_destroy(nfs_ctx *c)
+{
+    if (!c) return;
+    free_all(c);
+    delete c;
+}
+
+const char *nfs_strerror(int s)
+{
+    switch (s) {
+        case NFS_OK: return "ok";
+        case NFS_EINVAL: return "invalid argument";
+        case NFS_EUNSUPPORTED: return "unsupported frame shape";
+        case NFS_ENOMEM: return "out of memory";
+        case NFS_ECUDA: return "CUDA error";
+        case NFS_ESTATE: return "call not allowed in this state";
+        default: return "unknown status";
+    }
+}
+
+const char *nfs_last_error(const nfs_ctx *c) { return c ? c->errmsg.c_str() : ""; }
+
+void *nfs_get_stream(const nfs_ctx *c) { return c ? (void *)c->stream : nullptr; }
+
+int nfs_set_option(nfs_ctx *c, int key, int64_t v)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    switch (key) {
+        case NFS_OPT_TIMING: c->timing = v != 0; return NFS_OK;
+        case NFS_OPT_FFT_CHUNK:
+            if (v < 1 || v > kMaxChunk) return NFS_EINVAL;
+            c->fft_chunk = (int)v;
+            return NFS_OK;
+        case NFS_OPT_DELAY_VARIANT:
+            if (v < 0 || v > 8) return NFS_EINVAL;
+            c->delay_variant = (int)v;
+            return NFS_OK;
+        default: return NFS_EINVAL;
+    }
+}
+
+int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
+{
+    if (!c || !v) return NFS_EINVAL;
+    switch (key) {
+        case NFS_OPT_TIMING: *v = c->timing; return NFS_OK;
+        case NFS_OPT_BLOCK_FRAMES: *v = c->K; return NFS_OK;
+        case NFS_OPT_RING_SLOTS: *v = c->R; return NFS_OK;
+        case NFS_OPT_PITCH: *v = c->g.Wp; return NFS_OK;
+        case NFS_OPT_PATH: *v = c->path; return NFS_OK;
+        case NFS_OPT_FFT_CHUNK: *v = c->fft_chunk; return NFS_OK;
+        case NFS_OPT_DELAY_VARIANT: *v = c->delay_variant; return NFS_OK;
+        default: return NFS_EINVAL;
+    }
+}
+
+int nfs_get_timings(nfs_ctx *c, double *ms, int64_t *launches)
+{
+    int rc = nfs_synchronize(c);
+    if (rc) return rc;
+    for (int s = 0; s < NFS_N_STAGES; ++s) {
+        if (ms) ms[s] = c->stage_ms[s];
+        if (launches) launches[s] = c->stage_n[s];
+    }
+    return NFS_OK;
+}
+
+int nfs_reset_timings(nfs_ctx *c)
+{
+    int rc = nfs_synchronize(c);
+    if (rc) return rc;
+    for (int s = 0; s < NFS_N_STAGES; ++s) {
+        c->stage_ms[s] = 0.0;
+        c->stage_n[s] = 0;
+    }
+    return NFS_OK;
+}
+
+int64_t nfs_launch_count(const nfs_ctx *c) { return c ? c->launches : -1; }
+
+}  // extern "C"

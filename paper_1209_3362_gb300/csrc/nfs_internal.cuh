@@ -1,0 +1,96 @@
+// Internal declarations shared by the CUDA translation units of the NFS library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "nfs.h"
+
+namespace nfs {
+
+template <typename T>
+struct cplx_t;
+template <>
+struct cplx_t<float> {
+    using type = float2;
+};
+template <>
+struct cplx_t<double> {
+    using type = double2;
+};
+
+// FFT plan of one transform length: radices in stage order and the twiddle table
+// tw[m] = exp(-2 pi i m / L), m < L (built in FP64 on the host).
+constexpr int kMaxStages = 16;
+struct FftPlan {
+    int L = 0;
+    int nstages = 0;
+    int radix[kMaxStages] = {};
+};
+
+bool make_plan(int L, FftPlan *plan);  // false if L has a prime factor other than 2 or 3
+
+// One device-side description of the frame geometry.
+struct Geometry {
+    int H, W;      // frame size
+    int Lr;        // row transform length W/2
+    int Wh;        // W/2 + 1 non-redundant columns
+    int Wp;        // row pitch of spectra in HBM (complex values), Wp >= Wh, multiple of 4
+    size_t M;      // H * Wp: complex values per spectrum
+    size_t HW;     // pixels per frame
+};
+
+// --------------------------------------------------------------- launchers (stream-ordered)
+
+// sums[f] = sum of the pixels of frame f (exact, uint64) for f < nf.  sums must be zeroed.
+cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
+                              cudaStream_t s);
+
+// ref[x] = fl32(i_0(x) * fl32(HW / S_0)) : the FP32 normalised first frame.
+cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
+                             float *ref, cudaStream_t s);
+
+// Row pass: for nf frames, normalise (and subtract ref when T = float) and write the r2c row
+// transforms [H][Wp] into ring slots (slot0 + f) % R.
+template <typename T>
+cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
+                           const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
+                           const typename cplx_t<T>::type *tw_post, typename cplx_t<T>::type *ring, int R,
+                           int slot0, cudaStream_t s);
+
+// Column pass: in-place length-H transforms of the nf ring slots written by the row pass.
+template <typename T>
+cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
+                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s);
+
+// Fused FP32 delay update for new frames t0 .. t0+nb-1 (all already in the ring).
+struct DelayArgs {
+    const float2 *ring;
+    int R;
+    size_t M;
+    long long t0;
+    int nb;
+    const int *delays;
+    int nd;
+    float2 *acc;  // [nd][M] (Kahan sum, compensation)
+};
+cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
+
+// Plain FP64 update of one frame t.
+cudaError_t launch_delay_f64(const double2 *ring, int R, size_t M, long long t, const int *delays, int nd,
+                             double *acc, cudaStream_t s);
+
+// Binning: D[j][b] = sum_{i in bin b} w_i value_j(i) / (pairs_j * C_b).
+// modes: CSR by bin, entries (flat index << 1) | (weight == 2).
+template <typename Acc>
+cudaError_t launch_bin(const Acc *acc, size_t M, int nd, int nq, const int *bin_off, const int *bin_modes,
+                       const long long *pairs, const long long *counts, double *D, cudaStream_t s);
+
+// 2-D export: out[ky][kx] (kx < Wh) = value_j(ky*Wp + kx) / pairs.
+template <typename Acc>
+cudaError_t launch_export(const Acc *acc_j, const Geometry &g, long long pairs, double *out, cudaStream_t s);
+
+}  // namespace nfs

@@ -1,0 +1,175 @@
+"""Parity of the CUDA library with the FP64 oracle, element by element on the same seeded frames.
+
+Tolerance: the fused FP32 path must match the oracle to 2e-5 relative on every binned D_b(tau)
+whose bin and pair counts are non-zero; the plain FP64 path to 1e-12.  Bin and pair counts are
+integers and must match exactly.  Empty entries must be exactly 0.
+"""
+import numpy as np
+import pytest
+import torch
+
+import nfs_synth as S
+import paper_1209_3362_gb300 as P
+
+pytestmark = pytest.mark.gpu
+
+TOL_F32 = 2e-5
+TOL_F64 = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    torch.cuda.init()
+    P.build()
+    P.load_library()
+
+
+def rel_err(got, ref):
+    D, R = got["D"], ref["D"]
+    mask = (ref["bin_counts"][None, :] > 0) & (ref["pair_counts"][:, None] > 0)
+    assert np.all(D[~mask] == 0.0)
+    if not mask.any():
+        return 0.0
+    return float(np.max(np.abs(D[mask] - R[mask]) / np.abs(R[mask])))
+
+
+def check_counts(got, ref):
+    np.testing.assert_array_equal(got["bin_counts"], ref["bin_counts"])
+    np.testing.assert_array_equal(got["pair_counts"], ref["pair_counts"])
+    np.testing.assert_allclose(got["q_mean"], ref["q_mean"], rtol=1e-12, atol=0)
+
+
+def run_lib(frames, delays, nq, path="f32", block=0, chunks=None, device=False):
+    with P.NFS(frames.shape[1], frames.shape[2], delays, nq, path=path, block_frames=block) as ctx:
+        if device:
+            ctx.push_frames_device(torch.from_numpy(frames.view(np.int16)).cuda())
+        elif chunks is None:
+            ctx.push_frames(frames)
+        else:
+            o = 0
+            for c in chunks:
+                ctx.push_frames(frames[o:o + c])
+                o += c
+            assert o == frames.shape[0]
+        return ctx.structure_function()
+
+
+@pytest.fixture(scope="module")
+def ddm128(oracle_lib):
+    w = S.WORKLOADS["ddm128"]
+    fr = S.workload_source(w).frames_numpy(w.N)
+    ref = oracle_lib.structure_function(fr, w.delays, w.n_qbins)
+    return w, fr, ref
+
+
+def test_ddm128_full_fused_f32(ddm128):
+    w, fr, ref = ddm128
+    got = run_lib(fr, w.delays, w.n_qbins)
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F32
+
+
+def test_ddm128_full_plain_f64(ddm128):
+    w, fr, ref = ddm128
+    got = run_lib(fr, w.delays, w.n_qbins, path="f64")
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F64
+
+
+@pytest.mark.parametrize("block", [1, 5, 17, 32])
+def test_block_sizes(ddm128, block):
+    w, fr, ref = ddm128
+    got = run_lib(fr, w.delays, w.n_qbins, block=block)
+    assert rel_err(got, ref) <= TOL_F32
+
+
+def test_chunked_and_device_pushes_are_bit_identical(ddm128):
+    w, fr, ref = ddm128
+    a = run_lib(fr, w.delays, w.n_qbins)
+    b = run_lib(fr, w.delays, w.n_qbins, chunks=[1, 7, 33, 2, 64, 50, 43])
+    c = run_lib(fr, w.delays, w.n_qbins, device=True)
+    np.testing.assert_array_equal(a["D"], b["D"])
+    np.testing.assert_array_equal(a["D"], c["D"])
+
+
+def test_running_result_and_reset(oracle_lib):
+    fr = S.OUFrameSource(64, 96, 1.0, seed=21).frames_numpy(90)
+    delays = [1, 2, 3, 7, 20, 41, 60]
+    with P.NFS(64, 96, delays, 24) as ctx:
+        ctx.push_frames(fr[:37])
+        r1 = ctx.structure_function()
+        assert rel_err(r1, oracle_lib.structure_function(fr[:37], delays, 24)) <= TOL_F32
+        ctx.push_frames(fr[37:])
+        r2 = ctx.structure_function()
+        assert rel_err(r2, oracle_lib.structure_function(fr, delays, 24)) <= TOL_F32
+        ctx.reset()
+        ctx.push_frames(fr[10:70])
+        r3 = ctx.structure_function()
+        assert rel_err(r3, oracle_lib.structure_function(fr[10:70], delays, 24)) <= TOL_F32
+        assert ctx.frame_count == 60
+
+
+@pytest.mark.parametrize("H,W,nq,N,delays", [
+    (8, 8, 4, 12, [0, 1, 2, 5, 11, 30]),
+    (6, 8, 3, 9, [1, 2, 8]),
+    (12, 16, 8, 20, [0, 1, 3, 19]),
+    (6, 6, 3, 7, [1, 2]),
+    (2, 2, 1, 5, [1, 2]),
+    (16, 12, 40, 10, [1, 4]),
+    (48, 64, 24, 40, [1, 2, 3, 4, 5, 10, 39]),
+])
+def test_edge_shapes(oracle_lib, H, W, nq, N, delays):
+    fr = S.uniform_frames(N, H, W, seed=H * 1000 + W)
+    ref = oracle_lib.structure_function(fr, delays, nq)
+    for path, tol in (("f32", TOL_F32), ("f64", TOL_F64)):
+        got = run_lib(fr, delays, nq, path=path)
+        check_counts(got, ref)
+        assert rel_err(got, ref) <= tol, path
+        if delays[0] == 0:
+            assert np.all(got["D"][0] == 0.0)
+
+
+def test_identical_frames_give_exact_zero():
+    fr = np.repeat(S.uniform_frames(1, 32, 32, seed=5), 40, axis=0)
+    got = run_lib(fr, [1, 2, 17, 39, 45], 16)
+    assert np.all(got["D"] == 0.0)
+    assert list(got["pair_counts"]) == [39, 38, 23, 1, 0]
+
+
+@pytest.mark.parametrize("H,W", [(384, 512), (96, 768), (768, 1024)])
+def test_radix3_shapes(oracle_lib, H, W):
+    fr = S.OUFrameSource(H, W, 2.0, seed=H + W).frames_numpy(10)
+    delays = [1, 2, 5, 9]
+    nq = min(H, W) // 2
+    ref = oracle_lib.structure_function(fr, delays, nq)
+    got = run_lib(fr, delays, nq)
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F32
+
+
+def test_export_spectrum_matches_oracle_2d(oracle_lib):
+    fr = S.OUFrameSource(32, 48, 1.0, seed=31).frames_numpy(40)
+    delays = [1, 4, 13]
+    ref = oracle_lib.structure_function(fr, delays, 16, want_2d=True)
+    with P.NFS(32, 48, delays, 16) as ctx:
+        ctx.push_frames(fr)
+        for j in range(len(delays)):
+            got = ctx.export_spectrum(j)
+            R = ref["D2d"][j]
+            scale = np.mean(R)
+            err = np.abs(got - R) / (np.abs(R) + 1e-3 * scale)
+            assert err.max() <= 1e-4, (j, err.max())
+
+
+def test_ddm1024_subset(oracle_lib):
+    """Full 1024x1024 frames (the single-sequence workload's shape) on a short sequence."""
+    w = S.WORKLOADS["ddm1024"]
+    N = 24
+    fr = S.OUFrameSource(w.H, w.W, w.Dc, seed=w.seed, device="cuda", dtype=torch.float32).frames_numpy(N)
+    delays = [d for d in w.delays if d < N][:: 3] + [N - 1]
+    delays = sorted(set(delays))
+    ref = oracle_lib.structure_function(fr, delays, w.n_qbins)
+    got = run_lib(fr, delays, w.n_qbins)
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F32

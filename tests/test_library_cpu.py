@@ -1,0 +1,71 @@
+"""Host-side checks of the CUDA library that need no GPU: it loads, exports every symbol the public
+header declares, and rejects bad arguments before touching the device."""
+import ctypes
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import paper_1209_3362_gb300 as P
+
+
+@pytest.fixture(scope="module")
+def lib():
+    P.build()
+    return P.load_library()
+
+
+def test_exports_every_header_symbol(lib):
+    names = P.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the dynamic symbol table agrees (extern "C", unmangled)
+    out = subprocess.run(["nm", "-D", "--defined-only", P.LIB_PATH], capture_output=True, text=True).stdout
+    exported = {line.split()[-1] for line in out.splitlines() if " T " in line}
+    assert set(names) <= exported
+
+
+def _create(lib, H, W, delays, nq, path=0, block=0):
+    h = ctypes.c_void_p()
+    d = np.ascontiguousarray(np.asarray(delays, np.int32))
+    rc = lib.nfs_create_ex(H, W, d.ctypes.data if d.size else None, d.size, nq, path, block, ctypes.byref(h))
+    return rc, h
+
+
+@pytest.mark.parametrize("H,W", [(10, 64), (64, 10), (7, 8), (8, 7), (64, 8192), (0, 8), (5 * 64, 64),
+                                 (64, 2 * 5)])
+def test_rejects_unsupported_shapes(lib, H, W):
+    rc, h = _create(lib, H, W, [1, 2], 8)
+    assert rc in (P.NFS_EUNSUPPORTED, P.NFS_EINVAL) and not h.value
+
+
+@pytest.mark.parametrize("delays,nq,path,block", [([2, 1], 8, 0, 0), ([1, 1], 8, 0, 0), ([-1, 2], 8, 0, 0),
+                                                  ([], 8, 0, 0), ([1, 2], 0, 0, 0), ([1, 2], 8, 7, 0),
+                                                  ([1, 2], 8, 0, 33), ([1, 70000], 8, 0, 0)])
+def test_rejects_bad_arguments(lib, delays, nq, path, block):
+    rc, h = _create(lib, 64, 64, delays, nq, path, block)
+    assert rc == P.NFS_EINVAL and not h.value
+
+
+def test_null_safety_and_status_text(lib):
+    lib.nfs_destroy(None)
+    assert lib.nfs_strerror(P.NFS_EUNSUPPORTED) == b"unsupported frame shape"
+    assert lib.nfs_strerror(P.NFS_ECUDA) == b"CUDA error"
+    assert lib.nfs_push_frames(None, None, 1) == P.NFS_EINVAL
+    assert lib.nfs_structure_function(None, None, None, None, None) == P.NFS_EINVAL
+    assert lib.nfs_frame_count(None) == -1
+    assert lib.nfs_create(64, 64, None, 2, 8, ctypes.byref(ctypes.c_void_p())) == P.NFS_EINVAL
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The package never imports the oracle: the product path has no CPU route."""
+    import paper_1209_3362_gb300
+    src_dir = os.path.dirname(paper_1209_3362_gb300.__file__)
+    for root, _, files in os.walk(src_dir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(root, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text and "nfsor_" not in text, f
