@@ -9,7 +9,8 @@
 //                into the W/2+1 non-redundant outputs X[k] = E[k] + exp(-2 pi i k / W) O[k] with
 //                E = (Z[k] + conj Z[W/2-k]) / 2 and O = (Z[k] - conj Z[W/2-k]) / 2i.  The input
 //                pixels are normalised on load: p = i / <i> (FP64 path), or
-//                p = fl32(fl32(i * fl32(1/<i>)) - r) with the FP32 reference image r (FP32 path).
+//                p = i / <i> - r with the FP32 reference image r, 1/<i> carried as a float pair and
+//                the subtraction fused so that only p itself is rounded (FP32 path).
 //   column pass  each group of CB adjacent columns of the slot is transformed along y in place.
 //
 // Stockham stage of radix R on a length-L transform whose sub-transforms have length Ns so far:
@@ -152,7 +153,10 @@ __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ fr
     const int row0 = blockIdx.x * rpc;
     const unsigned long long S = sums[f];
     const double invd = S ? (double)g.HW / (double)S : 0.0;
-    const float invf = (float)invd;
+    // 1/<i> as an unevaluated float pair hi + lo: rounding 1/<i> to one float would scale the frame
+    // by (1 + d), d ~ 1e-8, and leak d times the beam's large low-q spectrum into the differences.
+    const float inv_hi = (float)invd;
+    const float inv_lo = (float)(invd - (double)inv_hi);
     const uint16_t *fr = frames + (size_t)f * g.HW;
 
     for (int e = threadIdx.x; e < rpc * L; e += blockDim.x) {
@@ -163,8 +167,11 @@ __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ fr
             const size_t o = (size_t)y * g.W + 2 * m;
             const uint16_t a = fr[o], b = fr[o + 1];
             if (sizeof(T) == 4) {
-                z.x = (T)__fsub_rn(__fmul_rn((float)a, invf), __ldg(ref + o));
-                z.y = (T)__fsub_rn(__fmul_rn((float)b, invf), __ldg(ref + o + 1));
+                // p = i (hi + lo) - r with the subtraction inside the first fused multiply-add, so
+                // only the small result p is rounded
+                const float fa = (float)a, fb = (float)b;
+                z.x = (T)__fmaf_rn(fa, inv_lo, __fmaf_rn(fa, inv_hi, -__ldg(ref + o)));
+                z.y = (T)__fmaf_rn(fb, inv_lo, __fmaf_rn(fb, inv_hi, -__ldg(ref + o + 1)));
             } else {
                 z.x = (T)((double)a * invd);
                 z.y = (T)((double)b * invd);

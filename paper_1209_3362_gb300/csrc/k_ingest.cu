@@ -51,15 +51,15 @@ cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g,
     return cudaGetLastError();
 }
 
-// ref[x] = fl32( i_0(x) * fl32(HW / S_0) ), rounded products without contraction so the row pass
-// reproduces it exactly for frame 0 (its normalised-and-shifted image is then exactly 0).
+// ref[x] = fl32(i_0(x) / <i_0>): the first normalised frame.  Any fixed image would do (it cancels
+// in every difference); this one removes the static beam before the FP32 transform.
 __global__ void k_reference(const uint16_t *__restrict__ frame0, const unsigned long long *__restrict__ sum0,
                             size_t HW, float *__restrict__ ref)
 {
     unsigned long long S = *sum0;
-    float inv = S ? (float)((double)HW / (double)S) : 0.0f;
+    double inv = S ? (double)HW / (double)S : 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += (size_t)gridDim.x * blockDim.x)
-        ref[i] = __fmul_rn((float)frame0[i], inv);
+        ref[i] = (float)((double)frame0[i] * inv);
 }
 
 cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,

@@ -49,7 +49,7 @@ struct Geometry {
 cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
                               cudaStream_t s);
 
-// ref[x] = fl32(i_0(x) * fl32(HW / S_0)) : the FP32 normalised first frame.
+// ref[x] = fl32(i_0(x) / <i_0>): the FP32 normalised first frame.
 cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
                              float *ref, cudaStream_t s);
 

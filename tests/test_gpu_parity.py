@@ -29,6 +29,9 @@ def rel_err(got, ref):
     D, R = got["D"], ref["D"]
     mask = (ref["bin_counts"][None, :] > 0) & (ref["pair_counts"][:, None] > 0)
     assert np.all(D[~mask] == 0.0)
+    zero = mask & (R == 0.0)  # tau = 0 or identical frames: exact zero on both sides
+    assert np.all(D[zero] == 0.0)
+    mask &= R != 0.0
     if not mask.any():
         return 0.0
     return float(np.max(np.abs(D[mask] - R[mask]) / np.abs(R[mask])))
