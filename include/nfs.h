@@ -45,6 +45,7 @@ extern "C" {
 #define NFS_ENOMEM (-3)       /* device or pinned host allocation failed */
 #define NFS_ECUDA (-4)        /* a CUDA call or kernel failed (sticky) */
 #define NFS_ESTATE (-5)       /* call not allowed in the context's current state */
+#define NFS_ETOOBIG (-6)      /* problem needs more than the no-allocation scratch (see below) */
 
 /* Arithmetic of the analysis path. */
 #define NFS_PATH_FUSED_F32 0 /* FP32 frames and spectra, blocked fused delay update, Kahan-FP32
@@ -164,6 +165,39 @@ int nfs_reset_timings(nfs_ctx *ctx);
  * Number of kernel launches the context has issued since creation (all stages, both paths).
  */
 int64_t nfs_launch_count(const nfs_ctx *ctx);
+
+/*
+ * ---------------------------------------------------------------- analysis without allocation
+ * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
+ * device memory while they run: a process whose device memory is owned by another allocator
+ * (a framework's pool that has reserved the GPU), or an acquisition loop that must not take the
+ * device-wide synchronisation that cudaMalloc / cudaFree can imply.
+ *
+ * nfs_structure_function_noalloc() computes, in one call, what nfs_create + nfs_push_frames_device
+ * + nfs_structure_function compute for the fused FP32 path (same kernels, block K = 32), but
+ * takes all of its scratch (spectrum ring, accumulators, twiddles, bin table, sums) from one
+ * static device array of NFS_NOALLOC_SCRATCH_BYTES, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   dev_frames   n_frames frames in DEVICE memory, [n_frames][H][W] uint16, 2-byte aligned
+ *   H, W, delays, n_delays, n_qbins   as for nfs_create (delays and outputs are HOST memory)
+ *   stream       cudaStream_t to run on (NULL = the legacy default stream); synchronised on return
+ *   D, bin_counts, pair_counts        as for nfs_structure_function
+ * Returns NFS_ETOOBIG, before any GPU work, when the sizes need more scratch than the array holds:
+ * about 8 (tau_max + 32 + n_delays) H (W/2 + 1) bytes plus small tables (for example 128 x 128
+ * frames with tau_max = 50 and 50 delays need about 9 MB).
+ * Notes for callers:
+ *   - The array is a file-scope __device__ variable: every GPU that loads this library holds
+ *     NFS_NOALLOC_SCRATCH_BYTES of device memory for it until the process exits.
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the one array and it keeps the previous call's contents (the call clears
+ *     what must start at zero).  Calls that overlap on the GPU -- two host threads, or two
+ *     streams -- race on it and give wrong results; serialise them.
+ */
+#define NFS_NOALLOC_SCRATCH_BYTES (64ull << 20)
+int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_frames, int H, int W, const int32_t *delays,
+                                   int n_delays, int n_qbins, void *stream, double *D, int64_t *bin_counts,
+                                   int64_t *pair_counts);
 
 #ifdef __cplusplus
 }

@@ -24,6 +24,8 @@ NFS_EUNSUPPORTED = -2
 NFS_ENOMEM = -3
 NFS_ECUDA = -4
 NFS_ESTATE = -5
+NFS_ETOOBIG = -6
+NOALLOC_SCRATCH_BYTES = 64 << 20
 PATH_FUSED_F32 = 0
 PATH_PLAIN_F64 = 1
 OPT_TIMING = 1
@@ -79,6 +81,7 @@ def load_library(path: Optional[str] = None):
         "nfs_get_timings": (I, [V, V, V]),
         "nfs_reset_timings": (I, [V]),
         "nfs_launch_count": (I64, [V]),
+        "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -101,7 +104,8 @@ def status_text(status: int) -> str:
         return load_library().nfs_strerror(status).decode()
     except Exception:
         return {0: "ok", -1: "invalid argument", -2: "unsupported frame shape", -3: "out of memory",
-                -4: "CUDA error", -5: "call not allowed in this state"}.get(status, "unknown status")
+                -4: "CUDA error", -5: "call not allowed in this state",
+                -6: "problem too large for the no-allocation scratch"}.get(status, "unknown status")
 
 
 def _ptr(a):
@@ -227,3 +231,24 @@ class NFS:
 
     def reset_timings(self):
         self._check(self._L.nfs_reset_timings(self._h), "nfs_reset_timings")
+
+
+def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) -> dict:
+    """One-shot analysis of device frames that allocates no device memory (its scratch is a fixed
+    static array in the library; see nfs_structure_function_noalloc in include/nfs.h).
+
+    frames: CUDA tensor [n, H, W] of 2-byte integers.  Calls on one device must not overlap.
+    """
+    L = load_library()
+    assert frames.is_cuda and frames.is_contiguous() and frames.element_size() == 2 and frames.dim() == 3
+    n, H, W = frames.shape
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    D = np.zeros((d.size, int(n_qbins)), np.float64)
+    bc = np.zeros(int(n_qbins), np.int64)
+    pc = np.zeros(d.size, np.int64)
+    rc = L.nfs_structure_function_noalloc(ctypes.c_void_p(frames.data_ptr()), int(n), int(H), int(W), _ptr(d),
+                                          int(d.size), int(n_qbins), ctypes.c_void_p(stream or None), _ptr(D),
+                                          _ptr(bc), _ptr(pc))
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_structure_function_noalloc")
+    return dict(D=D, bin_counts=bc, pair_counts=pc)

@@ -629,6 +629,7 @@ const char *nfs_strerror(int s)
         case NFS_ENOMEM: return "out of memory";
         case NFS_ECUDA: return "CUDA error";
         case NFS_ESTATE: return "call not allowed in this state";
+        case NFS_ETOOBIG: return "problem too large for the no-allocation scratch";
         default: return "unknown status";
     }
 }
