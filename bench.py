@@ -187,6 +187,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS))
     ap.add_argument("--frames", type=int, default=0, help="override N (smaller runs; not a bench value)")
+    ap.add_argument("--H", type=int, default=0, help="override frame height (profiling cases; not a bench value)")
+    ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
@@ -194,9 +196,9 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     w = S.WORKLOADS[args.workload]
-    if args.frames:
+    if args.frames or args.H or args.W:
         import dataclasses
-        w = dataclasses.replace(w, N=args.frames)
+        w = dataclasses.replace(w, N=args.frames or w.N, H=args.H or w.H, W=args.W or w.W)
     if args.impl == "reference":
         return run_reference(args, w)
 

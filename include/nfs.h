@@ -46,6 +46,7 @@ extern "C" {
 #define NFS_ECUDA (-4)        /* a CUDA call or kernel failed (sticky) */
 #define NFS_ESTATE (-5)       /* call not allowed in the context's current state */
 #define NFS_ETOOBIG (-6)      /* problem needs more than the no-allocation scratch (see below) */
+#define NFS_ETIMEOUT (-7)     /* a bounded wait inside a kernel gave up (sticky, like NFS_ECUDA) */
 
 /* Arithmetic of the analysis path. */
 #define NFS_PATH_FUSED_F32 0 /* FP32 frames and spectra, blocked fused delay update, Kahan-FP32
@@ -70,7 +71,7 @@ int nfs_create(int H, int W, const int32_t *delays, int n_delays, int n_qbins, n
 
 /*
  * Same as nfs_create with an explicit path (NFS_PATH_*) and block size K (frames per fused delay
- * update; 0 = library default).  The plain FP64 path ignores K (it updates once per frame).
+ * update, 1..256; 0 = the default 256).  The plain FP64 path ignores K (it updates once per frame).
  */
 int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block_frames,
                   nfs_ctx **out);
@@ -136,11 +137,11 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 /* Option keys for nfs_set_option / nfs_get_option. */
 #define NFS_OPT_TIMING 1      /* 1 = record CUDA events around every kernel launch (default 0) */
 #define NFS_OPT_BLOCK_FRAMES 2 /* read-only: K */
-#define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K */
+#define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K (FP32) or tau_max + 64 (FP64) */
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
 #define NFS_OPT_PATH 5         /* read-only: NFS_PATH_* */
 #define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..64; default 4) */
-#define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel variant (0 = default) */
+#define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel: 0 = tiled (default), 1 = one thread per mode */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);
 int nfs_get_option(const nfs_ctx *ctx, int key, int64_t *value);
 

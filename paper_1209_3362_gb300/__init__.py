@@ -25,6 +25,7 @@ NFS_ENOMEM = -3
 NFS_ECUDA = -4
 NFS_ESTATE = -5
 NFS_ETOOBIG = -6
+NFS_ETIMEOUT = -7
 NOALLOC_SCRATCH_BYTES = 64 << 20
 PATH_FUSED_F32 = 0
 PATH_PLAIN_F64 = 1
@@ -105,7 +106,7 @@ def status_text(status: int) -> str:
     except Exception:
         return {0: "ok", -1: "invalid argument", -2: "unsupported frame shape", -3: "out of memory",
                 -4: "CUDA error", -5: "call not allowed in this state",
-                -6: "problem too large for the no-allocation scratch"}.get(status, "unknown status")
+                -6: "problem too large for the no-allocation scratch", -7: "a device-side wait ran out of time"}.get(status, "unknown status")
 
 
 def _ptr(a):

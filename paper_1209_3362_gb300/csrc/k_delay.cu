@@ -7,6 +7,19 @@
 // and a squared modulus per mode instead of a transform ("only the square moduli of FFT
 // differences" of the processing paragraph).  Averaging over t at fixed tau is the time average
 // that stands for the ensemble average of Eq. 1 for stationary dynamics.
+//
+// Tiled kernel (variant 0).  One CTA owns a tile of 32 consecutive modes for a block of K = 256
+// new frames; 16 warps each take 16 consecutive frames (lane = mode), holding those 16 spectra in
+// registers.  Delays are taken in order as runs of consecutive values ("sub-runs" of up to 16):
+// for a run starting at d0 a warp keeps the 16 older values P_{t-d0} .. in a register window and
+// slides it back one frame per delay, so one shared-memory load serves 16 pairs; an isolated
+// delay costs one load per pair.  The tile's slots stream newest-to-oldest through a 512-slot
+// ring in shared memory, filled by bulk asynchronous copies (TMA, cp.async.bulk) that complete on
+// mbarriers, one copy group per stage, the next stage's group prefetched while the current one
+// computes when both fit.  Per-warp partial sums go through shared memory, are added in a fixed
+// warp order and then into the Kahan (sum, compensation) pair of the accumulator.
+#include <algorithm>
+
 #include "nfs_internal.cuh"
 
 namespace nfs {
@@ -21,8 +34,263 @@ __device__ __forceinline__ float2 kahan_add(float2 a, float p)
     return a;
 }
 
-// Fused FP32 update for a block of nb <= KB new frames t0 .. t0+nb-1.  One thread per mode k: the
-// block's spectra stay in registers, each delay adds a plain FP32 block partial into a Kahan pair.
+// ------------------------------------------------------------------ schedule (host)
+
+bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, std::vector<Stage> *sts)
+{
+    srs->clear();
+    sts->clear();
+    int j = 0;
+    while (j < nd && delays[j] == 0) ++j;  // tau = 0 pairs a frame with itself: D = 0 exactly
+    while (j < nd) {
+        const int j0 = j, d0 = delays[j];
+        int len = 1;
+        while (j0 + len < nd && len < 16 && delays[j0 + len] == d0 + len) ++len;
+        srs->push_back({j0, len, d0});
+        j = j0 + len;
+    }
+    const int K = kDelayBlock, SB = kSlotBuf, SPAN = 64;
+    int lo_prev = 0;     // frames t0 + lo_prev .. are in the buffer after the new block is loaded
+    int dmin_prev = 0;   // the new block itself is the "previous" range of stage 0
+    size_t r = 0;
+    while (r < srs->size()) {
+        Stage st;
+        st.sr0 = (int)r;
+        const int dmin = (*srs)[r].d0;
+        int dmax = dmin + (*srs)[r].len - 1;
+        size_t e = r + 1;
+        while (e < srs->size() && (*srs)[e].d0 + (*srs)[e].len - 1 - dmin <= SPAN) {
+            dmax = (*srs)[e].d0 + (*srs)[e].len - 1;
+            ++e;
+        }
+        st.nsr = (int)(e - r);
+        // load only what this stage needs and is not loaded yet (a large first delay or a large gap
+        // must not pull in unneeded frames: a group never exceeds K + SPAN slots)
+        st.lo = -dmax;
+        st.hi = std::min(lo_prev - 1, K - 1 - dmin);
+        if (K + dmax - dmin > SB) return false;  // cannot happen with SPAN = 64
+        st.prefetch = (sts->empty() ? 0 : (K + dmax - dmin_prev <= SB)) ? 1 : 0;
+        if (st.lo <= st.hi) lo_prev = st.lo;
+        dmin_prev = dmin;
+        sts->push_back(st);
+        r = e;
+    }
+    return true;
+}
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ unsigned smem_u32(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for the phase of a copy group; gives up after limit_ns (returns false).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
+                                                  unsigned long long limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+// ------------------------------------------------------------------ tiled kernel
+
+constexpr int kWarps = 16;  // warps per CTA
+constexpr int kTw = 16;     // consecutive frames per warp
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+static_assert(kWarps * kTw == kDelayBlock, "block = warps x frames per warp");
+
+struct TiledSmem {
+    float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf
+    float red[16][kWarps][kTile];          // per-warp partial sums of up to 16 pending delays
+    int jd[16];                            // delay indices of the pending partials
+    unsigned long long bar[2];             // copy-group barriers
+};
+
+// Issue the bulk copies of frames t0+lo .. t0+hi of this tile into the slot ring (thread 0 only).
+__device__ __forceinline__ void issue_group(TiledSmem &S, const float2 *__restrict__ ring, int R, size_t tile,
+                                            long long t0, int lo, int hi, unsigned long long *bar)
+{
+    const long long a0 = t0 + lo, b = t0 + hi;
+    const unsigned bytes = (lo <= hi) ? (unsigned)((hi - lo + 1) * kTile * sizeof(float2)) : 0u;
+    mbar_expect_tx(bar, bytes);
+    long long a = a0;
+    while (a <= b) {
+        const int rs = (int)(((a % R) + R) % R);
+        const int bp = (int)(a & (kSlotBuf - 1));
+        long long n = b - a + 1;
+        n = n < (long long)(R - rs) ? n : (long long)(R - rs);
+        n = n < (long long)(kSlotBuf - bp) ? n : (long long)(kSlotBuf - bp);
+        bulk_g2s(&S.buf[bp][0], ring + ((tile * (size_t)R + (size_t)rs) * kTile), (unsigned)(n * kTile * sizeof(float2)),
+                 bar);
+        a += n;
+    }
+}
+
+// One sub-run of consecutive delays d0 .. d0+len-1 for the warp's frames ta .. ta+15.
+template <bool MASK>
+__device__ __forceinline__ void subrun(TiledSmem &S, const float2 (&xt)[kTw], int lane, int warp, int ta, int d0,
+                                       int len, int pend, int hi_lim)
+{
+    float2 w[kTw];
+#pragma unroll
+    for (int i = 0; i < kTw; ++i) w[i] = S.buf[(ta + i - d0) & (kSlotBuf - 1)][lane];
+#pragma unroll
+    for (int uu = 0; uu < 16; ++uu) {
+        if (uu >= len) break;
+        const int tau = d0 + uu;
+        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+        for (int i = 0; i < kTw; ++i) {
+            const float2 y = w[(i - uu) & (kTw - 1)];
+            const float dr = xt[i].x - y.x, di = xt[i].y - y.y;
+            if (MASK) {
+                const bool v = (i >= tau - ta) && (i < hi_lim);
+                const float q = fmaf(dr, dr, di * di);
+                if (i & 1)
+                    p1 += v ? q : 0.f;
+                else
+                    p0 += v ? q : 0.f;
+            } else {
+                if (i & 1) {
+                    p1 = fmaf(dr, dr, p1);
+                    p3 = fmaf(di, di, p3);
+                } else {
+                    p0 = fmaf(dr, dr, p0);
+                    p2 = fmaf(di, di, p2);
+                }
+            }
+        }
+        S.red[pend + uu][warp][lane] = (p0 + p1) + (p2 + p3);
+        if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = S.buf[(ta - tau - 1) & (kSlotBuf - 1)][lane];
+    }
+}
+
+__device__ __forceinline__ void flush_partials(TiledSmem &S, float2 *__restrict__ acc, size_t M, size_t tile, int pend)
+{
+    __syncthreads();
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j < pend) {
+        float s = 0.f;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) s += S.red[j][w][lane];
+        float2 *a = acc + (size_t)S.jd[j] * M + tile * kTile + lane;
+        *a = kahan_add(*a, s);
+    }
+    __syncthreads();
+}
+
+template <bool MASK>
+__global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
+                                                                    long long t0, int nb,
+                                                                    const SubRun *__restrict__ subruns,
+                                                                    const Stage *__restrict__ stages, int nstages,
+                                                                    float2 *__restrict__ acc, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
+    const size_t tile = blockIdx.x;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
+    const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
+
+    if (tid == 0) {
+        mbar_init(&S.bar[0], 1);
+        mbar_init(&S.bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // group 0: the block's own frames t0 .. t0 + K - 1
+    if (tid == 0) issue_group(S, ring, R, tile, t0, 0, kDelayBlock - 1, &S.bar[0]);
+    bool ok = mbar_wait_bounded(&S.bar[0], 0, kWaitLimitNs);
+    if (__syncthreads_or(!ok)) {
+        if (tid == 0) atomicExch(err, 1);
+        return;
+    }
+    float2 xt[kTw];
+#pragma unroll
+    for (int i = 0; i < kTw; ++i) xt[i] = S.buf[(ta + i) & (kSlotBuf - 1)][lane];
+    __syncthreads();
+
+    int pend = 0;
+    for (int s = 0; s < nstages; ++s) {
+        const Stage st = stages[s];
+        const int g = s + 1;  // copy group of stage s
+        if (tid == 0) {
+            if (!st.prefetch) issue_group(S, ring, R, tile, t0, st.lo, st.hi, &S.bar[g & 1]);
+            if (s + 1 < nstages) {
+                const Stage nx = stages[s + 1];
+                if (nx.prefetch) issue_group(S, ring, R, tile, t0, nx.lo, nx.hi, &S.bar[(g + 1) & 1]);
+            }
+        }
+        ok = mbar_wait_bounded(&S.bar[g & 1], (unsigned)((g >> 1) & 1), kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // let copies still in flight land (bounded) before the CTA's shared memory goes away
+                mbar_wait_bounded(&S.bar[(g + 1) & 1], (unsigned)(((g + 1) >> 1) & 1), kWaitLimitNs / 20);
+            }
+            return;
+        }
+        for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
+            const SubRun sr = subruns[r];
+            if (pend + sr.len > 16) {
+                flush_partials(S, acc, M, tile, pend);
+                pend = 0;
+            }
+            if (tid < sr.len) S.jd[pend + tid] = sr.j0 + tid;
+            subrun<MASK>(S, xt, lane, warp, ta, sr.d0, sr.len, pend, hi_lim);
+            pend += sr.len;
+        }
+        __syncthreads();
+    }
+    if (pend) flush_partials(S, acc, M, tile, pend);
+}
+
+// ------------------------------------------------------------------ simple block kernel (variant 1)
+
+// One thread per mode: the block's spectra stay in registers, each delay adds a plain FP32 block
+// partial into a Kahan pair.  Used for blocks of up to 32 frames and as a cross-check.
 template <int KB>
 __global__ void __launch_bounds__(256) k_delay_f32_block(const float2 *__restrict__ ring, int R, size_t M,
                                                          int base_slot, long long t0, int nb,
@@ -37,7 +305,7 @@ __global__ void __launch_bounds__(256) k_delay_f32_block(const float2 *__restric
         if (i < nb) {
             int sl = base_slot + i;
             if (sl >= R) sl -= R;
-            x[i] = ring[(size_t)sl * M + k];
+            x[i] = ring[ring_index(sl, k, R)];
         }
     }
     const long long tlast = t0 + nb - 1;
@@ -51,7 +319,7 @@ __global__ void __launch_bounds__(256) k_delay_f32_block(const float2 *__restric
                 int sl = base_slot + i - tau;
                 if (sl < 0) sl += R;
                 if (sl >= R) sl -= R;
-                const float2 y = ring[(size_t)sl * M + k];
+                const float2 y = ring[ring_index(sl, k, R)];
                 const float dr = x[i].x - y.x, di = x[i].y - y.y;
                 p = fmaf(dr, dr, p);
                 p = fmaf(di, di, p);
@@ -66,16 +334,44 @@ constexpr int kBlockMax = 32;
 
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
 {
-    (void)variant;
     if (a.nb <= 0) return cudaSuccess;
-    if (a.nb > kBlockMax) return cudaErrorInvalidValue;
-    const int base = (int)(a.t0 % a.R);
-    const unsigned grid = (unsigned)((a.M + 255) / 256);
-    k_delay_f32_block<kBlockMax><<<grid, 256, 0, s>>>(a.ring, a.R, a.M, base, a.t0, a.nb, a.delays, a.nd, a.acc);
+    if (variant == 1 || !a.stages) {
+        // simple kernel, in sub-blocks of up to 32 frames (all frames of the block are in the ring)
+        for (int o = 0; o < a.nb; o += kBlockMax) {
+            const int nb = std::min(kBlockMax, a.nb - o);
+            const long long t0 = a.t0 + o;
+            const int base = (int)(t0 % a.R);
+            const unsigned grid = (unsigned)((a.M + 255) / 256);
+            k_delay_f32_block<kBlockMax><<<grid, 256, 0, s>>>(a.ring, a.R, a.M, base, t0, nb, a.delays, a.nd, a.acc);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    if (a.nb > kDelayBlock || (a.M % kTile) != 0) return cudaErrorInvalidValue;
+    if (a.nstages == 0) return cudaSuccess;  // only tau = 0 in the list
+    const size_t smem = sizeof(TiledSmem);
+    const bool mask = (a.t0 < (long long)a.tau_max) || (a.nb < kDelayBlock);
+    const unsigned grid = (unsigned)(a.M / kTile);
+    if (mask) {
+        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_delay_f32_tiled<true><<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, a.subruns, a.stages,
+                                                                 a.nstages, a.acc, a.err);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_delay_f32_tiled<false><<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, a.subruns, a.stages,
+                                                                  a.nstages, a.acc, a.err);
+    }
     return cudaGetLastError();
 }
 
-// Plain FP64 path: one frame t per launch, FP64 accumulators, no blocking.
+// ------------------------------------------------------------------ plain FP64 path
+
+// One frame t per launch, FP64 accumulators, no blocking; slot-major ring [R][M].
 __global__ void __launch_bounds__(256) k_delay_f64(const double2 *__restrict__ ring, int R, size_t M, int tslot,
                                                    long long t, const int *__restrict__ delays, int nd,
                                                    double *__restrict__ acc)

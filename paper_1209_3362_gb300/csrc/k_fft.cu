@@ -13,6 +13,9 @@
 //                the subtraction fused so that only p itself is rounded (FP32 path).
 //   column pass  each group of CB adjacent columns of the slot is transformed along y in place.
 //
+// The FP32 ring is tile-major (see ring_index: 32-mode tiles, each with its slots contiguous);
+// the FP64 ring of the plain path is slot-major [R][M].
+//
 // Stockham stage of radix R on a length-L transform whose sub-transforms have length Ns so far:
 // butterfly j < L/R reads x[j + r L/R] (r < R), twists input r by exp(-2 pi i (j mod Ns) r / (Ns R)),
 // applies an R-point DFT and writes output r to (j / Ns) Ns R + (j mod Ns) + r Ns.
@@ -135,7 +138,7 @@ __device__ C *fft_all(C *a, C *b, const FftPlan &plan, int nb, int is, int bs, c
     return a;
 }
 
-template <typename T>
+template <typename T, bool TILED>
 __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ frames,
                                                  const unsigned long long *__restrict__ sums,
                                                  const float *__restrict__ ref, Geometry g, FftPlan plan,
@@ -182,7 +185,7 @@ __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ fr
     __syncthreads();
     C *Z = fft_all<C, false>(bufA, bufB, plan, rpc, 1, L, tw);
 
-    C *spec = ring + (size_t)((slot0 + f) % R) * g.M;
+    const int slot = (slot0 + f) % R;
     const T half = (T)0.5;
     for (int e = threadIdx.x; e < rpc * g.Wp; e += blockDim.x) {
         const int r = e / g.Wp, k = e - r * g.Wp;
@@ -198,11 +201,12 @@ __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ fr
             const C O = {half * d.y, -half * d.x};  // (zk - zc) / 2i
             X = cadd(E, cmul(__ldg(twp + k), O));
         }
-        spec[(size_t)y * g.Wp + k] = X;
+        const size_t kk = (size_t)y * g.Wp + k;
+        ring[TILED ? ring_index(slot, kk, R) : (size_t)slot * g.M + kk] = X;
     }
 }
 
-template <typename T>
+template <typename T, bool TILED>
 __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
                                                  const typename cplx_t<T>::type *__restrict__ tw,
                                                  typename cplx_t<T>::type *__restrict__ ring, int R, int slot0,
@@ -215,18 +219,22 @@ __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
     C *bufB = bufA + (size_t)H * CB;
     const int f = blockIdx.y;
     const int x0 = blockIdx.x * CB;
-    C *spec = ring + (size_t)((slot0 + f) % R) * g.M;
+    const int slot = (slot0 + f) % R;
+    auto at = [&](int y, int x) -> size_t {
+        const size_t kk = (size_t)y * g.Wp + x;
+        return TILED ? ring_index(slot, kk, R) : (size_t)slot * g.M + kk;
+    };
     for (int e = threadIdx.x; e < H * CB; e += blockDim.x) {
         const int y = e / CB, c = e - y * CB;
         const int x = x0 + c;
-        bufA[e] = (x < g.Wp) ? spec[(size_t)y * g.Wp + x] : C{(T)0, (T)0};
+        bufA[e] = (x < g.Wp) ? ring[at(y, x)] : C{(T)0, (T)0};
     }
     __syncthreads();
     C *Y = fft_all<C, true>(bufA, bufB, plan, CB, CB, 1, tw);
     for (int e = threadIdx.x; e < H * CB; e += blockDim.x) {
         const int y = e / CB, c = e - y * CB;
         const int x = x0 + c;
-        if (x < g.Wp) spec[(size_t)y * g.Wp + x] = Y[e];
+        if (x < g.Wp) ring[at(y, x)] = Y[e];
     }
 }
 
@@ -249,11 +257,13 @@ cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long l
     const int rpc = row_rows_per_cta(g);
     const size_t smem = 2 * (size_t)rpc * g.Lr * sizeof(C);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_row_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_row_fft<T, sizeof(T) == 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.H + rpc - 1) / rpc, nf);
-    k_row_fft<T><<<grid, 256, smem, s>>>(frames, sums, ref, g, plan, tw_row, tw_post, ring, R, slot0, rpc);
+    k_row_fft<T, sizeof(T) == 4><<<grid, 256, smem, s>>>(frames, sums, ref, g, plan, tw_row, tw_post, ring, R, slot0,
+                                                          rpc);
     return cudaGetLastError();
 }
 
@@ -275,11 +285,12 @@ cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const
     const int cb = col_block(g, sizeof(C));
     const size_t smem = 2 * (size_t)g.H * cb * sizeof(C);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_col_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_col_fft<T, sizeof(T) == 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.Wp + cb - 1) / cb, nf);
-    k_col_fft<T><<<grid, 256, smem, s>>>(g, plan, tw_col, ring, R, slot0, cb);
+    k_col_fft<T, sizeof(T) == 4><<<grid, 256, smem, s>>>(g, plan, tw_col, ring, R, slot0, cb);
     return cudaGetLastError();
 }
 

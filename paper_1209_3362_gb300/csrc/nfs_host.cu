@@ -13,8 +13,8 @@ using namespace nfs;
 
 namespace {
 
-constexpr int kDefaultBlock = 32;   // K: frames per fused delay update
-constexpr int kMaxBlock = 32;       // largest K the fused kernel takes
+constexpr int kDefaultBlock = kDelayBlock;  // K: frames per fused delay update
+constexpr int kMaxBlock = kDelayBlock;      // largest K the fused kernel takes
 constexpr int kMaxChunk = 64;       // largest FFT chunk
 constexpr int kMaxDim = 4096;
 constexpr int kMaxDelay = 65536;
@@ -80,6 +80,10 @@ struct nfs_ctx {
     int *d_bin_off = nullptr, *d_bin_modes = nullptr;
     long long *d_pairs = nullptr, *d_counts = nullptr;
     double *d_D = nullptr, *d_export = nullptr;
+    SubRun *d_subruns = nullptr;
+    Stage *d_stages = nullptr;
+    int nstages = 0;
+    int *d_err = nullptr;
 
     std::vector<long long> counts, pairs_h;
     std::vector<double> qmean;
@@ -273,6 +277,9 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_counts);
     cudaFree(c->d_D);
     cudaFree(c->d_export);
+    cudaFree(c->d_subruns);
+    cudaFree(c->d_stages);
+    cudaFree(c->d_err);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
@@ -301,6 +308,11 @@ int flush_block(nfs_ctx *c)
     a.delays = c->d_delays;
     a.nd = c->nd;
     a.acc = (float2 *)c->d_acc;
+    a.subruns = c->d_subruns;
+    a.stages = c->d_stages;
+    a.nstages = c->nstages;
+    a.err = c->d_err;
+    a.tau_max = c->tau_max;
     int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
                    "delay_f32");
     if (rc) return rc;
@@ -405,7 +417,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     c->g.Lr = W / 2;
     c->g.Wh = W / 2 + 1;
     c->g.Wp = (c->g.Wh + 3) / 4 * 4;
-    c->g.M = (size_t)H * c->g.Wp;
+    c->g.M = ((size_t)H * c->g.Wp + kTile - 1) / kTile * kTile;
     c->g.HW = (size_t)H * W;
     c->R = c->tau_max + (c->f32() ? c->K : kMaxChunk);
     c->stage_frames = (int)std::max<size_t>(1, std::min<size_t>(kMaxChunk, (64u << 20) / c->frame_bytes()));
@@ -451,6 +463,20 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
             return bail(NFS_ECUDA);
     }
     if (build_bins(c)) return bail(NFS_ECUDA);
+    if ((rc = alloc_dev(c, (void **)&c->d_err, sizeof(int)))) return bail(rc);
+    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) return bail(NFS_ECUDA);
+    if (c->f32()) {
+        std::vector<SubRun> srs;
+        std::vector<Stage> sts;
+        if (!build_delay_schedule(c->delays.data(), c->nd, &srs, &sts)) return bail(NFS_EUNSUPPORTED);
+        c->nstages = (int)sts.size();
+        if ((rc = alloc_dev(c, (void **)&c->d_subruns, sizeof(SubRun) * std::max<size_t>(srs.size(), 1)))) return bail(rc);
+        if ((rc = alloc_dev(c, (void **)&c->d_stages, sizeof(Stage) * std::max<size_t>(sts.size(), 1)))) return bail(rc);
+        if (!srs.empty() && cudaMemcpy(c->d_subruns, srs.data(), sizeof(SubRun) * srs.size(), cudaMemcpyHostToDevice))
+            return bail(NFS_ECUDA);
+        if (!sts.empty() && cudaMemcpy(c->d_stages, sts.data(), sizeof(Stage) * sts.size(), cudaMemcpyHostToDevice))
+            return bail(NFS_ECUDA);
+    }
     *out = c;
     return NFS_OK;
 }
@@ -561,7 +587,14 @@ int nfs_structure_function(nfs_ctx *c, double *D, int64_t *bin_counts, int64_t *
     }, "bin");
     if (rc) return rc;
     CK(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * (size_t)c->nd * c->nq, cudaMemcpyDeviceToHost, c->stream));
+    int dev_err = 0;
+    CK(c, cudaMemcpyAsync(&dev_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    if (dev_err) {
+        c->errmsg = "delay kernel: a bounded wait for its shared-memory copies gave up";
+        if (c->err == NFS_OK) c->err = NFS_ETIMEOUT;
+        return c->err;
+    }
     for (int b = 0; b < c->nq; ++b) bin_counts[b] = c->counts[b];
     for (int j = 0; j < c->nd; ++j) pair_counts[j] = c->pairs_h[j];
     if (q_mean)
@@ -630,6 +663,7 @@ const char *nfs_strerror(int s)
         case NFS_ECUDA: return "CUDA error";
         case NFS_ESTATE: return "call not allowed in this state";
         case NFS_ETOOBIG: return "problem too large for the no-allocation scratch";
+        case NFS_ETIMEOUT: return "a device-side wait ran out of time";
         default: return "unknown status";
     }
 }

@@ -39,7 +39,7 @@ struct Geometry {
     int Lr;        // row transform length W/2
     int Wh;        // W/2 + 1 non-redundant columns
     int Wp;        // row pitch of spectra in HBM (complex values), Wp >= Wh, multiple of 4
-    size_t M;      // H * Wp: complex values per spectrum
+    size_t M;      // complex values per spectrum: H * Wp rounded up to a multiple of 32
     size_t HW;     // pixels per frame
 };
 
@@ -54,7 +54,7 @@ cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *s
                              float *ref, cudaStream_t s);
 
 // Row pass: for nf frames, normalise (and subtract ref when T = float) and write the r2c row
-// transforms [H][Wp] into ring slots (slot0 + f) % R.
+// transforms [H][Wp] into ring slots (slot0 + f) % R (tile-major for float, slot-major for double).
 template <typename T>
 cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                            const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
@@ -66,16 +66,46 @@ template <typename T>
 cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
                            typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s);
 
+// Layout of the FP32 spectrum ring: tiles of 32 consecutive modes (flat k = ky * Wp + kx), each
+// tile holding its R slots contiguously, [tile][slot][32] float2, so the time series of a tile is
+// one contiguous run of memory (a slot range is one bulk copy).
+constexpr int kTile = 32;
+__host__ __device__ __forceinline__ size_t ring_index(int slot, size_t k, int R)
+{
+    return ((k >> 5) * (size_t)R + (size_t)slot) * kTile + (k & (kTile - 1));
+}
+
+// Schedule of the tiled delay kernel (built on the host from the delay list, fixed per context).
+// A sub-run is up to 16 consecutive delays d0 .. d0+len-1 (delay indices j0 .. j0+len-1); a stage
+// is a group of sub-runs whose ring slots are loaded together.  Slot offsets are relative to the
+// first frame t0 of the block: stage s loads frames t0+lo .. t0+hi (hi < the previous stage's lo).
+struct SubRun {
+    int j0, len, d0;
+};
+struct Stage {
+    int sr0, nsr;    // sub-runs sr0 .. sr0+nsr-1
+    int lo, hi;      // frames t0+lo .. t0+hi to load (lo > hi: nothing new)
+    int prefetch;    // 1: its loads may be issued while the previous stage computes
+};
+constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
+constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
+bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
+
 // Fused FP32 delay update for new frames t0 .. t0+nb-1 (all already in the ring).
 struct DelayArgs {
-    const float2 *ring;
+    const float2 *ring;  // tile-major, see ring_index
     int R;
-    size_t M;
+    size_t M;            // modes per spectrum (multiple of 32) = accumulator row stride
     long long t0;
     int nb;
     const int *delays;
     int nd;
     float2 *acc;  // [nd][M] (Kahan sum, compensation)
+    const SubRun *subruns;
+    const Stage *stages;
+    int nstages;
+    int *err;     // device status word: set when a bounded wait in the kernel gives up
+    int tau_max;
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
 

@@ -174,7 +174,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     g.Lr = W / 2;
     g.Wh = W / 2 + 1;
     g.Wp = (g.Wh + 3) / 4 * 4;
-    g.M = (size_t)H * g.Wp;
+    g.M = ((size_t)H * g.Wp + kTile - 1) / kTile * kTile;
     g.HW = (size_t)H * W;
     FftPlan prow, pcol;
     if (!make_plan(g.Lr, &prow) || !make_plan(H, &pcol)) return NFS_EUNSUPPORTED;
@@ -238,8 +238,9 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
         NA_CK(launch_col_fft<float>(nf, g, pcol, twc, ring, R, slot0, s));
         done += nf;
         if (done - processed == kNaBlock || done == n_frames) {
-            DelayArgs a{ring, R, g.M, processed, (int)(done - processed), dd, nd, acc};
-            NA_CK(launch_delay_f32(a, 0, s));
+            DelayArgs a{ring, R, g.M, processed, (int)(done - processed), dd, nd, acc, nullptr, nullptr, 0, nullptr,
+                        delays[nd - 1]};
+            NA_CK(launch_delay_f32(a, 1, s));  // the one-thread-per-mode kernel: blocks of 32 frames
             processed = done;
         }
     }

@@ -176,3 +176,48 @@ def test_ddm1024_subset(oracle_lib):
     got = run_lib(fr, delays, w.n_qbins)
     check_counts(got, ref)
     assert rel_err(got, ref) <= TOL_F32
+
+
+def _with_variant(frames, delays, nq, variant):
+    with P.NFS(frames.shape[1], frames.shape[2], delays, nq) as ctx:
+        ctx.set_option(P.OPT_DELAY_VARIANT, variant)
+        ctx.push_frames(frames)
+        return ctx.structure_function()
+
+
+@pytest.fixture(scope="module")
+def long64(oracle_lib):
+    """900 frames of 64x64 with log delays to 300: full 256-frame blocks after the first tau_max
+    frames (the unmasked steady-state kernel) and a ring of 556 slots that wraps."""
+    fr = S.OUFrameSource(64, 64, 1.0, gamma0=0.01, seed=51).frames_numpy(900)
+    delays = S.log_delays(1, 300, 60)
+    return fr, delays, oracle_lib.structure_function(fr, delays, 32)
+
+
+def test_tiled_steady_state_and_ring_wrap(long64):
+    fr, delays, ref = long64
+    with P.NFS(64, 64, delays, 32) as ctx:
+        assert ctx.get_option(P.OPT_BLOCK_FRAMES) == 256
+        assert ctx.get_option(P.OPT_RING_SLOTS) == 300 + 256 < fr.shape[0]
+        ctx.push_frames(fr)
+        got = ctx.structure_function()
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F32
+
+
+def test_delay_kernel_variants_agree(long64):
+    fr, delays, ref = long64
+    a = _with_variant(fr, delays, 32, 0)
+    b = _with_variant(fr, delays, 32, 1)
+    assert rel_err(a, ref) <= TOL_F32 and rel_err(b, ref) <= TOL_F32
+    np.testing.assert_allclose(a["D"], b["D"], rtol=2e-6, atol=0)
+
+
+def test_sparse_delays_with_large_gaps(oracle_lib):
+    """Gaps wider than the shared-memory slot ring allows to prefetch across."""
+    fr = S.OUFrameSource(32, 32, 3.0, seed=52).frames_numpy(1300)
+    delays = [1, 2, 3, 400, 401, 900, 1250]
+    ref = oracle_lib.structure_function(fr, delays, 16)
+    got = run_lib(fr, delays, 16)
+    check_counts(got, ref)
+    assert rel_err(got, ref) <= TOL_F32
