@@ -189,6 +189,7 @@ def main():
     ap.add_argument("--frames", type=int, default=0, help="override N (smaller runs; not a bench value)")
     ap.add_argument("--H", type=int, default=0, help="override frame height (profiling cases; not a bench value)")
     ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
+    ap.add_argument("--delays", type=int, default=0, help="use delays 1..n (profiling cases; not a bench value)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
@@ -196,9 +197,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
     w = S.WORKLOADS[args.workload]
-    if args.frames or args.H or args.W:
+    if args.frames or args.H or args.W or args.delays:
         import dataclasses
-        w = dataclasses.replace(w, N=args.frames or w.N, H=args.H or w.H, W=args.W or w.W)
+        w = dataclasses.replace(w, N=args.frames or w.N, H=args.H or w.H, W=args.W or w.W,
+                                delays=tuple(range(1, args.delays + 1)) if args.delays else w.delays)
     if args.impl == "reference":
         return run_reference(args, w)
 
