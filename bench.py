@@ -285,7 +285,7 @@ def main():
     per_launch_ms = delay_ms / max(delay_n, 1)
     achieved = (alg_bytes / n_launch) / (per_launch_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_delay_f32_block",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_delay_f32_tiled",
                 "peak_source": f"{peak_src} hbm_gbs", "bytes_per_launch": alg_bytes / n_launch,
                 "launch_ms": per_launch_ms}
     stage_ms = {k: v[0] / args.steps for k, v in tim.items()}

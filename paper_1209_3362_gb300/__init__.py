@@ -36,6 +36,7 @@ OPT_PITCH = 4
 OPT_PATH = 5
 OPT_FFT_CHUNK = 6
 OPT_DELAY_VARIANT = 7
+OPT_FFT_GENERIC = 8
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
 
 _lib = None

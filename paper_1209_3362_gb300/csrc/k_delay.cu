@@ -167,42 +167,85 @@ __device__ __forceinline__ void issue_group(TiledSmem &S, const float2 *__restri
     }
 }
 
-// One sub-run of consecutive delays d0 .. d0+len-1 for the warp's frames ta .. ta+15.
-template <bool MASK>
-__device__ __forceinline__ void subrun(TiledSmem &S, const float2 (&xt)[kTw], int lane, int warp, int ta, int d0,
-                                       int len, int pend, int hi_lim)
+// Packed FP32 pairs (Blackwell f32x2 arithmetic): a complex value is one 64-bit register
+// {re, im}; the difference and the squared-modulus accumulation are one instruction each.
+typedef unsigned long long pk_t;
+__device__ __forceinline__ pk_t psub(pk_t a, pk_t b)
 {
-    float2 w[kTw];
+    pk_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ pk_t psq_acc(pk_t d, pk_t acc)  // acc + {d.re^2, d.im^2}
+{
+    pk_t r;
+    asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
+    return r;
+}
+__device__ __forceinline__ float phsum(pk_t a)
+{
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+    return lo + hi;
+}
+
+// One sub-run of consecutive delays d0 .. d0+len-1 for the warp's frames ta .. ta+15, with
+// base = ta - d0: the pair (ta + i, d0 + u) reads frame base + i - u.  The window holds the 16
+// older values of the current delay; moving to the next delay drops the newest and loads one
+// older frame.  MASKED: drop pairs whose older frame is < 0 or whose new frame lies past the
+// block (i >= hi_lim).  WRAP: the 31 slot rows touched wrap around the slot ring, so every
+// address is taken modulo; otherwise they are immediate offsets from one base address.
+template <bool MASKED, bool WRAP>
+__device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int base, int len,
+                                       int pend, int hi_lim)
+{
+    const float2 *col = &S.buf[0][lane];
+    const float2 *p0 = col + (size_t)((base & (kSlotBuf - 1)) * kTile);
+    auto ldf = [&](int off) -> pk_t {  // the value of frame base + off
+        const float2 *a = WRAP ? col + (size_t)(((base + off) & (kSlotBuf - 1)) * kTile) : p0 + off * kTile;
+        return *reinterpret_cast<const pk_t *>(a);
+    };
+    pk_t w[kTw];
 #pragma unroll
-    for (int i = 0; i < kTw; ++i) w[i] = S.buf[(ta + i - d0) & (kSlotBuf - 1)][lane];
+    for (int i = 0; i < kTw; ++i) w[i] = ldf(i);
 #pragma unroll
     for (int uu = 0; uu < 16; ++uu) {
         if (uu >= len) break;
-        const int tau = d0 + uu;
-        float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+        pk_t a0 = 0ull, a1 = 0ull;
 #pragma unroll
         for (int i = 0; i < kTw; ++i) {
-            const float2 y = w[(i - uu) & (kTw - 1)];
-            const float dr = xt[i].x - y.x, di = xt[i].y - y.y;
-            if (MASK) {
-                const bool v = (i >= tau - ta) && (i < hi_lim);
-                const float q = fmaf(dr, dr, di * di);
-                if (i & 1)
-                    p1 += v ? q : 0.f;
-                else
-                    p0 += v ? q : 0.f;
-            } else {
-                if (i & 1) {
-                    p1 = fmaf(dr, dr, p1);
-                    p3 = fmaf(di, di, p3);
-                } else {
-                    p0 = fmaf(dr, dr, p0);
-                    p2 = fmaf(di, di, p2);
-                }
+            pk_t d = psub(xt[i], w[(i - uu) & (kTw - 1)]);
+            if (MASKED) {
+                const bool v = (i - uu >= -base) && (i < hi_lim);
+                d = v ? d : 0ull;
             }
+            if (i & 1)
+                a1 = psq_acc(d, a1);
+            else
+                a0 = psq_acc(d, a0);
         }
-        S.red[pend + uu][warp][lane] = (p0 + p1) + (p2 + p3);
-        if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = S.buf[(ta - tau - 1) & (kSlotBuf - 1)][lane];
+        S.red[pend + uu][warp][lane] = phsum(a0) + phsum(a1);
+        if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = ldf(-uu - 1);
+    }
+}
+
+// Picks the sub-run variant for this warp (the choice is uniform within the warp).
+__device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int ta,
+                                                int d0, int len, int pend, int hi_lim)
+{
+    const int base = ta - d0;
+    if (hi_lim <= 0 || base + kTw - 1 < 0) {  // no pair of this warp is valid
+        for (int u = 0; u < len; ++u) S.red[pend + u][warp][lane] = 0.f;
+        return;
+    }
+    if (base - (len - 1) >= 0 && hi_lim >= kTw) {
+        const int r0 = base & (kSlotBuf - 1);
+        if (r0 >= 16 && r0 + 15 < kSlotBuf)
+            subrun<false, false>(S, xt, lane, warp, base, len, pend, hi_lim);
+        else
+            subrun<false, true>(S, xt, lane, warp, base, len, pend, hi_lim);
+    } else {
+        subrun<true, true>(S, xt, lane, warp, base, len, pend, hi_lim);
     }
 }
 
@@ -220,11 +263,9 @@ __device__ __forceinline__ void flush_partials(TiledSmem &S, float2 *__restrict_
     __syncthreads();
 }
 
-template <bool MASK>
 __global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
                                                                     long long t0, int nb,
-                                                                    const SubRun *__restrict__ subruns,
-                                                                    const Stage *__restrict__ stages, int nstages,
+                                                                    const __grid_constant__ DelaySchedule sched,
                                                                     float2 *__restrict__ acc, int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -247,19 +288,20 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2
         if (tid == 0) atomicExch(err, 1);
         return;
     }
-    float2 xt[kTw];
+    pk_t xt[kTw];
 #pragma unroll
-    for (int i = 0; i < kTw; ++i) xt[i] = S.buf[(ta + i) & (kSlotBuf - 1)][lane];
+    for (int i = 0; i < kTw; ++i) xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane]);
     __syncthreads();
 
     int pend = 0;
-    for (int s = 0; s < nstages; ++s) {
-        const Stage st = stages[s];
+    const int nst = sched.nst;
+    for (int s = 0; s < nst; ++s) {
+        const Stage st = sched.st[s];
         const int g = s + 1;  // copy group of stage s
         if (tid == 0) {
             if (!st.prefetch) issue_group(S, ring, R, tile, t0, st.lo, st.hi, &S.bar[g & 1]);
-            if (s + 1 < nstages) {
-                const Stage nx = stages[s + 1];
+            if (s + 1 < nst) {
+                const Stage nx = sched.st[s + 1];
                 if (nx.prefetch) issue_group(S, ring, R, tile, t0, nx.lo, nx.hi, &S.bar[(g + 1) & 1]);
             }
         }
@@ -273,13 +315,13 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2
             return;
         }
         for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
-            const SubRun sr = subruns[r];
+            const SubRun sr = sched.sr[r];
             if (pend + sr.len > 16) {
                 flush_partials(S, acc, M, tile, pend);
                 pend = 0;
             }
             if (tid < sr.len) S.jd[pend + tid] = sr.j0 + tid;
-            subrun<MASK>(S, xt, lane, warp, ta, sr.d0, sr.len, pend, hi_lim);
+            subrun_dispatch(S, xt, lane, warp, ta, sr.d0, sr.len, pend, hi_lim);
             pend += sr.len;
         }
         __syncthreads();
@@ -335,7 +377,7 @@ constexpr int kBlockMax = 32;
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
 {
     if (a.nb <= 0) return cudaSuccess;
-    if (variant == 1 || !a.stages) {
+    if (variant == 1 || !a.sched) {
         // simple kernel, in sub-blocks of up to 32 frames (all frames of the block are in the ring)
         for (int o = 0; o < a.nb; o += kBlockMax) {
             const int nb = std::min(kBlockMax, a.nb - o);
@@ -349,23 +391,12 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
         return cudaSuccess;
     }
     if (a.nb > kDelayBlock || (a.M % kTile) != 0) return cudaErrorInvalidValue;
-    if (a.nstages == 0) return cudaSuccess;  // only tau = 0 in the list
+    if (a.sched->nst == 0) return cudaSuccess;  // only tau = 0 in the list
     const size_t smem = sizeof(TiledSmem);
-    const bool mask = (a.t0 < (long long)a.tau_max) || (a.nb < kDelayBlock);
+    cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(a.M / kTile);
-    if (mask) {
-        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k_delay_f32_tiled<true><<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, a.subruns, a.stages,
-                                                                 a.nstages, a.acc, a.err);
-    } else {
-        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        k_delay_f32_tiled<false><<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, a.subruns, a.stages,
-                                                                  a.nstages, a.acc, a.err);
-    }
+    k_delay_f32_tiled<<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, *a.sched, a.acc, a.err);
     return cudaGetLastError();
 }
 

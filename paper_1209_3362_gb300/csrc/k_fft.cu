@@ -250,10 +250,17 @@ template <typename T>
 cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                            const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
                            const typename cplx_t<T>::type *tw_post, typename cplx_t<T>::type *ring, int R,
-                           int slot0, cudaStream_t s)
+                           int slot0, cudaStream_t s, bool generic_only)
 {
     using C = typename cplx_t<T>::type;
     if (nf <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (!generic_only) {
+            cudaError_t e = launch_row_fft_ct(frames, nf, sums, ref, g, tw_row, tw_post, ring, R, slot0, s);
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();
+        }
+    }
     const int rpc = row_rows_per_cta(g);
     const size_t smem = 2 * (size_t)rpc * g.Lr * sizeof(C);
     if (smem > 48 * 1024) {
@@ -278,10 +285,17 @@ static int col_block(const Geometry &g, size_t csize)
 
 template <typename T>
 cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
-                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s)
+                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s, bool generic_only)
 {
     using C = typename cplx_t<T>::type;
     if (nf <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (!generic_only) {
+            cudaError_t e = launch_col_fft_ct(nf, g, tw_col, ring, R, slot0, s);
+            if (e != cudaErrorNotSupported) return e;
+            cudaGetLastError();
+        }
+    }
     const int cb = col_block(g, sizeof(C));
     const size_t smem = 2 * (size_t)g.H * cb * sizeof(C);
     if (smem > 48 * 1024) {
@@ -296,14 +310,14 @@ cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const
 
 template cudaError_t launch_row_fft<float>(const uint16_t *, int, const unsigned long long *, const float *,
                                            const Geometry &, const FftPlan &, const float2 *, const float2 *,
-                                           float2 *, int, int, cudaStream_t);
+                                           float2 *, int, int, cudaStream_t, bool);
 template cudaError_t launch_row_fft<double>(const uint16_t *, int, const unsigned long long *, const float *,
                                             const Geometry &, const FftPlan &, const double2 *, const double2 *,
-                                            double2 *, int, int, cudaStream_t);
+                                            double2 *, int, int, cudaStream_t, bool);
 template cudaError_t launch_col_fft<float>(int, const Geometry &, const FftPlan &, const float2 *, float2 *, int,
-                                           int, cudaStream_t);
+                                           int, cudaStream_t, bool);
 template cudaError_t launch_col_fft<double>(int, const Geometry &, const FftPlan &, const double2 *, double2 *,
-                                            int, int, cudaStream_t);
+                                            int, int, cudaStream_t, bool);
 
 bool make_plan(int L, FftPlan *plan)
 {

@@ -1,0 +1,340 @@
+// Compile-time-specialised FP32 FFT passes for the common frame sizes (same transforms as the
+// generic kernels in k_fft.cu: unscaled forward DFT, rows as half-length complex transforms plus
+// the real-to-complex split, then columns in place; tile-major ring).
+//
+// With the transform length, radices and batch known at compile time every index is a shift or
+// a constant multiply, every per-thread loop unrolls, and each thread keeps several butterflies'
+// inputs in registers.  The column pass runs in place in one shared buffer (all butterfly inputs
+// of a stage are read into registers before any output is written), so three CTAs fit per SM.
+#include "nfs_internal.cuh"
+
+namespace nfs {
+namespace ct {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return {a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return {a.x - b.x, a.y - b.y}; }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ float2 cmi(float2 a) { return {a.y, -a.x}; }  // -i a
+
+template <int R>
+struct Dft;
+template <>
+struct Dft<2> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        const float2 a = v[0];
+        v[0] = cadd(a, v[1]);
+        v[1] = csub(a, v[1]);
+    }
+};
+template <>
+struct Dft<3> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        const float s = 0.86602540378443864676f;  // sin(2 pi / 3)
+        const float2 t1 = cadd(v[1], v[2]), t2 = csub(v[1], v[2]);
+        const float2 m = {v[0].x - 0.5f * t1.x, v[0].y - 0.5f * t1.y};
+        const float2 r = {s * t2.y, -s * t2.x};
+        v[0] = cadd(v[0], t1);
+        v[1] = cadd(m, r);
+        v[2] = csub(m, r);
+    }
+};
+template <>
+struct Dft<4> {
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        const float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+        const float2 t2 = cadd(v[1], v[3]), t3 = cmi(csub(v[1], v[3]));
+        v[0] = cadd(t0, t2);
+        v[2] = csub(t0, t2);
+        v[1] = cadd(t1, t3);
+        v[3] = csub(t1, t3);
+    }
+};
+template <>
+struct Dft<8> {
+    // two 4-point transforms of the even and odd inputs, joined with exp(-2 pi i k / 8)
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 e[4] = {v[0], v[2], v[4], v[6]};
+        float2 o[4] = {v[1], v[3], v[5], v[7]};
+        Dft<4>::run(e);
+        Dft<4>::run(o);
+        const float h = 0.70710678118654752440f;
+        const float2 o1 = {h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};    // (1 - i)/sqrt2 * o1
+        const float2 o2 = cmi(o[2]);                                          // -i * o2
+        const float2 o3 = {h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};   // (-1 - i)/sqrt2 * o3
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    }
+};
+
+template <int REM>
+struct Pick {
+    static constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
+};
+
+// One Stockham stage on NB transforms of length L (element (b, i) at b*L + i, or i*NB + b when
+// BFAST), NT threads.  INPLACE: in == out, all inputs are read before a barrier, then written.
+template <int L, int R, int NS, int NB, bool BFAST, bool INPLACE, int NT>
+__device__ __forceinline__ void stage(const float2 *in, float2 *out, const float2 *__restrict__ tw)
+{
+    constexpr int NBF = L / R;
+    constexpr int TOT = NB * NBF;
+    constexpr int PER = (TOT + NT - 1) / NT;
+    constexpr int TWS = L / (NS * R);
+    float2 v[PER][R];
+    int jj[PER], bb[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int g = threadIdx.x + p * NT;
+        int b, j;
+        if (BFAST) {
+            b = g % NB;
+            j = g / NB;
+        } else {
+            b = g / NBF;
+            j = g % NBF;
+        }
+        jj[p] = j;
+        bb[p] = b;
+        if (TOT % NT == 0 || g < TOT) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = j + r * NBF;
+                v[p][r] = in[BFAST ? i * NB + b : b * L + i];
+            }
+        }
+    }
+    if (INPLACE) __syncthreads();
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int g = threadIdx.x + p * NT;
+        if (TOT % NT == 0 || g < TOT) {
+            const int j = jj[p], b = bb[p];
+            const int k = j % NS;
+            if (NS > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tw + k * r * TWS));
+            }
+            Dft<R>::run(v[p]);
+            const int base = (j / NS) * NS * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = base + r * NS;
+                out[BFAST ? i * NB + b : b * L + i] = v[p][r];
+            }
+        }
+    }
+}
+
+template <int L, int NS, int NB, bool BFAST, bool INPLACE, int NT>
+__device__ __forceinline__ float2 *run_stages(float2 *a, float2 *b, const float2 *__restrict__ tw)
+{
+    if constexpr (NS >= L) {
+        return a;
+    } else {
+        constexpr int R = Pick<L / NS>::R;
+        stage<L, R, NS, NB, BFAST, INPLACE, NT>(a, INPLACE ? a : b, tw);
+        __syncthreads();
+        if constexpr (INPLACE)
+            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(a, b, tw);
+        else
+            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(b, a, tw);
+    }
+}
+
+constexpr int kNT = 256;
+
+// Rows per CTA: the largest power of two with RPC * L <= 2048 (a multiple of 256 for the sizes
+// instantiated below).
+__host__ __device__ constexpr int rows_per_cta(int L)
+{
+    int r = 1;
+    while (2 * r * L <= 2048) r *= 2;
+    return r;
+}
+
+// Row pass for frames of width W = 2L: RPC rows per CTA, 8 complex points per thread.
+template <int L>
+__global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__ frames,
+                                                    const unsigned long long *__restrict__ sums,
+                                                    const float *__restrict__ ref, Geometry g,
+                                                    const float2 *__restrict__ tw, const float2 *__restrict__ twp,
+                                                    float2 *__restrict__ ring, int R, int slot0)
+{
+    constexpr int RPC = rows_per_cta(L);
+    constexpr int N = RPC * L;
+    constexpr int PER = N / kNT;
+    static_assert(N % kNT == 0, "row batch must fill the CTA");
+    __shared__ __align__(16) float2 bufA[N];
+    __shared__ __align__(16) float2 bufB[N];
+    const int f = blockIdx.y;
+    const int row0 = blockIdx.x * RPC;
+    const unsigned long long S = sums[f];
+    const double invd = S ? (double)g.HW / (double)S : 0.0;
+    // 1/<i> as a float pair; the reference subtraction sits inside the first FMA (see k_fft.cu)
+    const float inv_hi = (float)invd;
+    const float inv_lo = (float)(invd - (double)inv_hi);
+    const uint16_t *fr = frames + (size_t)f * g.HW;
+    constexpr int W = 2 * L;
+    unsigned raw[PER];
+    float2 rf[PER];
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * kNT;
+        const int r = e / L, m = e % L;
+        const int y = row0 + r;
+        if (y < g.H) {
+            const size_t o = (size_t)y * W + 2 * m;
+            raw[p] = __ldg(reinterpret_cast<const unsigned *>(fr + o));
+            rf[p] = __ldg(reinterpret_cast<const float2 *>(ref + o));
+        } else {
+            raw[p] = 0u;
+            rf[p] = {0.f, 0.f};
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * kNT;
+        const float a = (float)(raw[p] & 0xffffu), b = (float)(raw[p] >> 16);
+        bufA[e] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -rf[p].x)),
+                   __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -rf[p].y))};
+    }
+    __syncthreads();
+    const float2 *Z = run_stages<L, 1, RPC, false, false, kNT>(bufA, bufB, tw);
+
+    const int slot = (slot0 + f) % R;
+    constexpr int WP = ((L + 1) + 3) / 4 * 4;
+    for (int e = threadIdx.x; e < RPC * WP; e += kNT) {
+        const int r = e / WP, k = e % WP;
+        const int y = row0 + r;
+        if (y >= g.H) continue;
+        float2 X = {0.f, 0.f};
+        if (k <= L) {
+            const float2 zk = Z[r * L + (k == L ? 0 : k)];
+            float2 zc = Z[r * L + (k == 0 ? 0 : L - k)];
+            zc.y = -zc.y;
+            const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
+            const float2 d = csub(zk, zc);
+            const float2 O = {0.5f * d.y, -0.5f * d.x};
+            X = cadd(E, cmul(__ldg(twp + k), O));
+        }
+        ring[ring_index(slot, (size_t)y * WP + k, R)] = X;
+    }
+}
+
+// Columns per CTA of the column pass: 4, or 2 at H = 2048 (keeps the butterflies in registers).
+__host__ __device__ constexpr int cols_per_cta(int H) { return H >= 2048 ? 2 : 4; }
+
+// Column pass for frames of height H: CB adjacent columns per CTA, in place.
+template <int H>
+__global__ void __launch_bounds__(kNT, 2) k_col_fft_ct(Geometry g, const float2 *__restrict__ tw,
+                                                    float2 *__restrict__ ring, int R, int slot0)
+{
+    constexpr int CB = cols_per_cta(H);
+    constexpr int N = H * CB;
+    constexpr int PER = N / kNT;
+    static_assert(N % kNT == 0, "column batch must fill the CTA");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    const int f = blockIdx.y;
+    const int x0 = blockIdx.x * CB;
+    const int slot = (slot0 + f) % R;
+    constexpr int CH = PER % 8 == 0 ? 8 : (PER % 6 == 0 ? 6 : (PER % 4 == 0 ? 4 : PER));  // loads in flight per thread
+    static_assert(PER % CH == 0, "chunked loads");
+#pragma unroll
+    for (int p0 = 0; p0 < PER; p0 += CH) {
+        float2 v[CH];
+#pragma unroll
+        for (int q = 0; q < CH; ++q) {
+            const int e = threadIdx.x + (p0 + q) * kNT;
+            const int y = e / CB, c = e % CB;
+            v[q] = ring[ring_index(slot, (size_t)y * g.Wp + x0 + c, R)];
+        }
+#pragma unroll
+        for (int q = 0; q < CH; ++q) buf[threadIdx.x + (p0 + q) * kNT] = v[q];
+    }
+    __syncthreads();
+    const float2 *Y = run_stages<H, 1, CB, true, true, kNT>(buf, buf, tw);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * kNT;
+        const int y = e / CB, c = e % CB;
+        ring[ring_index(slot, (size_t)y * g.Wp + x0 + c, R)] = Y[e];
+    }
+}
+
+}  // namespace ct
+
+template <int L>
+static cudaError_t row_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
+                          const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
+                          cudaStream_t s)
+{
+    constexpr int RPC = ct::rows_per_cta(L);
+    dim3 grid((g.H + RPC - 1) / RPC, nf);
+    ct::k_row_fft_ct<L><<<grid, ct::kNT, 0, s>>>(frames, sums, ref, g, tw, twp, ring, R, slot0);
+    return cudaGetLastError();
+}
+
+template <int H>
+static cudaError_t col_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0, cudaStream_t s)
+{
+    constexpr int CB = ct::cols_per_cta(H);
+    const size_t smem = (size_t)H * CB * sizeof(float2);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(ct::k_col_fft_ct<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    dim3 grid(g.Wp / CB, nf);
+    ct::k_col_fft_ct<H><<<grid, ct::kNT, smem, s>>>(g, tw, ring, R, slot0);
+    return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported when no specialised kernel exists for the size (the caller then
+// uses the generic kernel).
+cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
+                              const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
+                              cudaStream_t s)
+{
+    if ((reinterpret_cast<uintptr_t>(frames) & 3) || g.Wp != ((g.Lr + 1) + 3) / 4 * 4) return cudaErrorNotSupported;
+    switch (g.Lr) {
+        case 64: return row_ct<64>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 128: return row_ct<128>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 192: return row_ct<192>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 256: return row_ct<256>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 384: return row_ct<384>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 512: return row_ct<512>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 768: return row_ct<768>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 1024: return row_ct<1024>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 2048: return row_ct<2048>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0,
+                              cudaStream_t s)
+{
+    if (g.Wp % 4) return cudaErrorNotSupported;
+    switch (g.H) {
+        case 64: return col_ct<64>(nf, g, tw, ring, R, slot0, s);
+        case 128: return col_ct<128>(nf, g, tw, ring, R, slot0, s);
+        case 256: return col_ct<256>(nf, g, tw, ring, R, slot0, s);
+        case 384: return col_ct<384>(nf, g, tw, ring, R, slot0, s);
+        case 512: return col_ct<512>(nf, g, tw, ring, R, slot0, s);
+        case 768: return col_ct<768>(nf, g, tw, ring, R, slot0, s);
+        case 1024: return col_ct<1024>(nf, g, tw, ring, R, slot0, s);
+        case 2048: return col_ct<2048>(nf, g, tw, ring, R, slot0, s);
+        default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace nfs

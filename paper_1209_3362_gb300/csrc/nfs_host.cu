@@ -60,6 +60,7 @@ struct nfs_ctx {
     int fft_chunk = 4;
     int stage_frames = 1;
     int delay_variant = 0;
+    int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
     int device = 0;
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     std::vector<int32_t> delays;
@@ -80,9 +81,7 @@ struct nfs_ctx {
     int *d_bin_off = nullptr, *d_bin_modes = nullptr;
     long long *d_pairs = nullptr, *d_counts = nullptr;
     double *d_D = nullptr, *d_export = nullptr;
-    SubRun *d_subruns = nullptr;
-    Stage *d_stages = nullptr;
-    int nstages = 0;
+    DelaySchedule *sched = nullptr;  // tiled-kernel schedule (host copy, passed by value); NULL if too long
     int *d_err = nullptr;
 
     std::vector<long long> counts, pairs_h;
@@ -277,8 +276,7 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_counts);
     cudaFree(c->d_D);
     cudaFree(c->d_export);
-    cudaFree(c->d_subruns);
-    cudaFree(c->d_stages);
+    delete c->sched;
     cudaFree(c->d_err);
     if (c->stream) cudaStreamDestroy(c->stream);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
@@ -308,9 +306,7 @@ int flush_block(nfs_ctx *c)
     a.delays = c->d_delays;
     a.nd = c->nd;
     a.acc = (float2 *)c->d_acc;
-    a.subruns = c->d_subruns;
-    a.stages = c->d_stages;
-    a.nstages = c->nstages;
+    a.sched = c->sched;
     a.err = c->d_err;
     a.tau_max = c->tau_max;
     int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
@@ -337,12 +333,13 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
     if (c->f32()) {
         rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
             return launch_row_fft<float>(dsrc, nf, c->d_sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
-                                         (const float2 *)c->d_tw_post, (float2 *)c->d_ring, c->R, slot0, c->stream);
+                                         (const float2 *)c->d_tw_post, (float2 *)c->d_ring, c->R, slot0, c->stream,
+                                         c->fft_generic != 0);
         }, "row_fft_f32");
         if (rc) return rc;
         rc = timed(c, NFS_STAGE_COLFFT, c->stream, [&] {
             return launch_col_fft<float>(nf, c->g, c->plan_col, (const float2 *)c->d_tw_col, (float2 *)c->d_ring, c->R,
-                                         slot0, c->stream);
+                                         slot0, c->stream, c->fft_generic != 0);
         }, "col_fft_f32");
         if (rc) return rc;
         c->nframes += nf;
@@ -469,13 +466,15 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
         std::vector<SubRun> srs;
         std::vector<Stage> sts;
         if (!build_delay_schedule(c->delays.data(), c->nd, &srs, &sts)) return bail(NFS_EUNSUPPORTED);
-        c->nstages = (int)sts.size();
-        if ((rc = alloc_dev(c, (void **)&c->d_subruns, sizeof(SubRun) * std::max<size_t>(srs.size(), 1)))) return bail(rc);
-        if ((rc = alloc_dev(c, (void **)&c->d_stages, sizeof(Stage) * std::max<size_t>(sts.size(), 1)))) return bail(rc);
-        if (!srs.empty() && cudaMemcpy(c->d_subruns, srs.data(), sizeof(SubRun) * srs.size(), cudaMemcpyHostToDevice))
-            return bail(NFS_ECUDA);
-        if (!sts.empty() && cudaMemcpy(c->d_stages, sts.data(), sizeof(Stage) * sts.size(), cudaMemcpyHostToDevice))
-            return bail(NFS_ECUDA);
+        // a delay list too long for the parameter-space schedule uses the one-thread-per-mode kernel
+        if (srs.size() <= (size_t)kMaxSubRuns && sts.size() <= (size_t)kMaxSchedStages) {
+            c->sched = new (std::nothrow) DelaySchedule();
+            if (!c->sched) return bail(NFS_ENOMEM);
+            c->sched->nsr = (int)srs.size();
+            c->sched->nst = (int)sts.size();
+            std::copy(srs.begin(), srs.end(), c->sched->sr);
+            std::copy(sts.begin(), sts.end(), c->sched->st);
+        }
     }
     *out = c;
     return NFS_OK;
@@ -683,8 +682,12 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             c->fft_chunk = (int)v;
             return NFS_OK;
         case NFS_OPT_DELAY_VARIANT:
-            if (v < 0 || v > 8) return NFS_EINVAL;
+            if (v < 0 || v > 1) return NFS_EINVAL;
             c->delay_variant = (int)v;
+            return NFS_OK;
+        case NFS_OPT_FFT_GENERIC:
+            if (v < 0 || v > 1) return NFS_EINVAL;
+            c->fft_generic = (int)v;
             return NFS_OK;
         default: return NFS_EINVAL;
     }
@@ -701,6 +704,7 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_PATH: *v = c->path; return NFS_OK;
         case NFS_OPT_FFT_CHUNK: *v = c->fft_chunk; return NFS_OK;
         case NFS_OPT_DELAY_VARIANT: *v = c->delay_variant; return NFS_OK;
+        case NFS_OPT_FFT_GENERIC: *v = c->fft_generic; return NFS_OK;
         default: return NFS_EINVAL;
     }
 }

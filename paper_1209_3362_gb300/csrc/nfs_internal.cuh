@@ -59,12 +59,19 @@ template <typename T>
 cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                            const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
                            const typename cplx_t<T>::type *tw_post, typename cplx_t<T>::type *ring, int R,
-                           int slot0, cudaStream_t s);
+                           int slot0, cudaStream_t s, bool generic_only = false);
+
+// Compile-time-specialised FP32 passes (tile-major ring); cudaErrorNotSupported for sizes without one.
+cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
+                              const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
+                              cudaStream_t s);
+cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0,
+                              cudaStream_t s);
 
 // Column pass: in-place length-H transforms of the nf ring slots written by the row pass.
 template <typename T>
 cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
-                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s);
+                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s, bool generic_only = false);
 
 // Layout of the FP32 spectrum ring: tiles of 32 consecutive modes (flat k = ky * Wp + kx), each
 // tile holding its R slots contiguously, [tile][slot][32] float2, so the time series of a tile is
@@ -91,6 +98,15 @@ constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frame
 constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
 bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
 
+// The schedule travels by value in the kernel parameters (constant bank): uniform, cached reads.
+constexpr int kMaxSubRuns = 256;
+constexpr int kMaxSchedStages = 128;
+struct DelaySchedule {
+    int nsr, nst;
+    SubRun sr[kMaxSubRuns];
+    Stage st[kMaxSchedStages];
+};
+
 // Fused FP32 delay update for new frames t0 .. t0+nb-1 (all already in the ring).
 struct DelayArgs {
     const float2 *ring;  // tile-major, see ring_index
@@ -101,9 +117,7 @@ struct DelayArgs {
     const int *delays;
     int nd;
     float2 *acc;  // [nd][M] (Kahan sum, compensation)
-    const SubRun *subruns;
-    const Stage *stages;
-    int nstages;
+    const DelaySchedule *sched;  // host copy; NULL = no tiled schedule (one-thread-per-mode kernel)
     int *err;     // device status word: set when a bounded wait in the kernel gives up
     int tau_max;
 };

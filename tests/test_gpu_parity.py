@@ -221,3 +221,22 @@ def test_sparse_delays_with_large_gaps(oracle_lib):
     got = run_lib(fr, delays, 16)
     check_counts(got, ref)
     assert rel_err(got, ref) <= TOL_F32
+
+
+def test_specialised_and_generic_fft_agree_at_2048(oracle_lib):
+    """2048x2048 frames (the paper-scale shape): size-specialised FFT kernels vs the generic ones,
+    both against the oracle on a short sequence."""
+    N = 6
+    fr = S.OUFrameSource(2048, 2048, 1.0, gamma0=0.01, seed=61, device="cuda",
+                         dtype=torch.float32).frames_numpy(N)
+    delays = [1, 2, 5]
+    ref = oracle_lib.structure_function(fr, delays, 1024)
+    out = []
+    for generic in (0, 1):
+        with P.NFS(2048, 2048, delays, 1024) as ctx:
+            ctx.set_option(P.OPT_FFT_GENERIC, generic)
+            ctx.push_frames(fr)
+            out.append(ctx.structure_function())
+        check_counts(out[-1], ref)
+        assert rel_err(out[-1], ref) <= TOL_F32, generic
+    np.testing.assert_allclose(out[0]["D"], out[1]["D"], rtol=2e-6, atol=0)
