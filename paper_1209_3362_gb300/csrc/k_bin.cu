@@ -61,7 +61,7 @@ __global__ void k_export(const Acc *__restrict__ acc_j, Geometry g, long long pa
     const double inv = pairs > 0 ? 1.0 / (double)pairs : 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t ky = i / g.Wh, kx = i - ky * g.Wh;
-        out[i] = acc_value(acc_j, ky * g.Wp + kx) * inv;
+        out[i] = acc_value(acc_j, g.mode((int)kx, (int)ky)) * inv;
     }
 }
 

@@ -13,8 +13,9 @@
 //                the subtraction fused so that only p itself is rounded (FP32 path).
 //   column pass  each group of CB adjacent columns of the slot is transformed along y in place.
 //
-// The FP32 ring is tile-major (see ring_index: 32-mode tiles, each with its slots contiguous);
-// the FP64 ring of the plain path is slot-major [R][M].
+// FP32: the row pass writes a column-pair scratch, the column pass writes the tile-major ring (see
+// ring_index) in column-major mode order.  FP64: both passes work in place in the slot-major ring
+// [R][M] in row-major mode order.
 //
 // Stockham stage of radix R on a length-L transform whose sub-transforms have length Ns so far:
 // butterfly j < L/R reads x[j + r L/R] (r < R), twists input r by exp(-2 pi i (j mod Ns) r / (Ns R)),
@@ -138,14 +139,14 @@ __device__ C *fft_all(C *a, C *b, const FftPlan &plan, int nb, int is, int bs, c
     return a;
 }
 
-template <typename T, bool TILED>
+template <typename T>
 __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ frames,
                                                  const unsigned long long *__restrict__ sums,
                                                  const float *__restrict__ ref, Geometry g, FftPlan plan,
                                                  const typename cplx_t<T>::type *__restrict__ tw,
                                                  const typename cplx_t<T>::type *__restrict__ twp,
                                                  typename cplx_t<T>::type *__restrict__ ring, int R, int slot0,
-                                                 int rpc)
+                                                 int rpc, typename cplx_t<T>::type *__restrict__ scratch)
 {
     using C = typename cplx_t<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -201,16 +202,21 @@ __global__ void __launch_bounds__(256) k_row_fft(const uint16_t *__restrict__ fr
             const C O = {half * d.y, -half * d.x};  // (zk - zc) / 2i
             X = cadd(E, cmul(__ldg(twp + k), O));
         }
-        const size_t kk = (size_t)y * g.Wp + k;
-        ring[TILED ? ring_index(slot, kk, R) : (size_t)slot * g.M + kk] = X;
+        if (sizeof(T) == 4)
+            scratch[(size_t)f * g.H * g.Wp + g.scratch_index(k, y)] = X;
+        else
+            ring[(size_t)slot * g.M + (size_t)y * g.Wp + k] = X;
     }
 }
 
-template <typename T, bool TILED>
+// FP32: columns x0 .. x0+CB-1 read from the column-pair scratch, written to the tile-major ring in
+// column-major mode order (columns >= W/2+1 are padding and are dropped).  FP64: in place in the
+// slot-major ring.
+template <typename T>
 __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
                                                  const typename cplx_t<T>::type *__restrict__ tw,
                                                  typename cplx_t<T>::type *__restrict__ ring, int R, int slot0,
-                                                 int CB)
+                                                 int CB, const typename cplx_t<T>::type *__restrict__ scratch)
 {
     using C = typename cplx_t<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -220,21 +226,24 @@ __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
     const int f = blockIdx.y;
     const int x0 = blockIdx.x * CB;
     const int slot = (slot0 + f) % R;
-    auto at = [&](int y, int x) -> size_t {
-        const size_t kk = (size_t)y * g.Wp + x;
-        return TILED ? ring_index(slot, kk, R) : (size_t)slot * g.M + kk;
-    };
+    const C *src = scratch + (size_t)f * g.H * g.Wp;
     for (int e = threadIdx.x; e < H * CB; e += blockDim.x) {
         const int y = e / CB, c = e - y * CB;
         const int x = x0 + c;
-        bufA[e] = (x < g.Wp) ? ring[at(y, x)] : C{(T)0, (T)0};
+        C v = {(T)0, (T)0};
+        if (x < g.Wp) v = (sizeof(T) == 4) ? src[g.scratch_index(x, y)] : ring[(size_t)slot * g.M + (size_t)y * g.Wp + x];
+        bufA[e] = v;
     }
     __syncthreads();
     C *Y = fft_all<C, true>(bufA, bufB, plan, CB, CB, 1, tw);
     for (int e = threadIdx.x; e < H * CB; e += blockDim.x) {
         const int y = e / CB, c = e - y * CB;
         const int x = x0 + c;
-        if (x < g.Wp) ring[at(y, x)] = Y[e];
+        if (sizeof(T) == 4) {
+            if (x < g.Wh) ring[ring_index(slot, g.mode(x, y), R)] = Y[e];
+        } else if (x < g.Wp) {
+            ring[(size_t)slot * g.M + (size_t)y * g.Wp + x] = Y[e];
+        }
     }
 }
 
@@ -250,13 +259,13 @@ template <typename T>
 cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                            const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
                            const typename cplx_t<T>::type *tw_post, typename cplx_t<T>::type *ring, int R,
-                           int slot0, cudaStream_t s, bool generic_only)
+                           int slot0, cudaStream_t s, typename cplx_t<T>::type *scratch, const float2 *tws_row)
 {
     using C = typename cplx_t<T>::type;
     if (nf <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        if (!generic_only) {
-            cudaError_t e = launch_row_fft_ct(frames, nf, sums, ref, g, tw_row, tw_post, ring, R, slot0, s);
+        if (tws_row) {
+            cudaError_t e = launch_row_fft_ct(frames, nf, sums, ref, g, tws_row, tw_post, scratch, s);
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();
         }
@@ -264,13 +273,11 @@ cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long l
     const int rpc = row_rows_per_cta(g);
     const size_t smem = 2 * (size_t)rpc * g.Lr * sizeof(C);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_row_fft<T, sizeof(T) == 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_row_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.H + rpc - 1) / rpc, nf);
-    k_row_fft<T, sizeof(T) == 4><<<grid, 256, smem, s>>>(frames, sums, ref, g, plan, tw_row, tw_post, ring, R, slot0,
-                                                          rpc);
+    k_row_fft<T><<<grid, 256, smem, s>>>(frames, sums, ref, g, plan, tw_row, tw_post, ring, R, slot0, rpc, scratch);
     return cudaGetLastError();
 }
 
@@ -285,39 +292,55 @@ static int col_block(const Geometry &g, size_t csize)
 
 template <typename T>
 cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
-                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s, bool generic_only)
+                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s,
+                           const typename cplx_t<T>::type *scratch, const float2 *tws_col)
 {
     using C = typename cplx_t<T>::type;
     if (nf <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
-        if (!generic_only) {
-            cudaError_t e = launch_col_fft_ct(nf, g, tw_col, ring, R, slot0, s);
+        if (tws_col) {
+            cudaError_t e = launch_col_fft_ct(nf, g, tws_col, scratch, ring, R, slot0, s);
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();
         }
     }
-    const int cb = col_block(g, sizeof(C));
+    int cb = col_block(g, sizeof(C));
+    if (sizeof(T) == 4 && cb > 2) cb = 2;  // one scratch column pair per CTA
     const size_t smem = 2 * (size_t)g.H * cb * sizeof(C);
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_col_fft<T, sizeof(T) == 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k_col_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     dim3 grid((g.Wp + cb - 1) / cb, nf);
-    k_col_fft<T, sizeof(T) == 4><<<grid, 256, smem, s>>>(g, plan, tw_col, ring, R, slot0, cb);
+    k_col_fft<T><<<grid, 256, smem, s>>>(g, plan, tw_col, ring, R, slot0, cb, scratch);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_row_fft<float>(const uint16_t *, int, const unsigned long long *, const float *,
                                            const Geometry &, const FftPlan &, const float2 *, const float2 *,
-                                           float2 *, int, int, cudaStream_t, bool);
+                                           float2 *, int, int, cudaStream_t, float2 *, const float2 *);
 template cudaError_t launch_row_fft<double>(const uint16_t *, int, const unsigned long long *, const float *,
                                             const Geometry &, const FftPlan &, const double2 *, const double2 *,
-                                            double2 *, int, int, cudaStream_t, bool);
+                                            double2 *, int, int, cudaStream_t, double2 *, const float2 *);
 template cudaError_t launch_col_fft<float>(int, const Geometry &, const FftPlan &, const float2 *, float2 *, int,
-                                           int, cudaStream_t, bool);
+                                           int, cudaStream_t, const float2 *, const float2 *);
 template cudaError_t launch_col_fft<double>(int, const Geometry &, const FftPlan &, const double2 *, double2 *,
-                                            int, int, cudaStream_t, bool);
+                                            int, int, cudaStream_t, const double2 *, const float2 *);
+
+Geometry make_geometry(int H, int W, bool colmajor)
+{
+    Geometry g;
+    g.H = H;
+    g.W = W;
+    g.Lr = W / 2;
+    g.Wh = W / 2 + 1;
+    g.Wp = (g.Wh + 3) / 4 * 4;
+    g.HW = (size_t)H * W;
+    g.colmajor = colmajor ? 1 : 0;
+    const size_t m = colmajor ? (size_t)g.Wh * H : (size_t)H * g.Wp;
+    g.M = (m + kTile - 1) / kTile * kTile;
+    return g;
+}
 
 bool make_plan(int L, FftPlan *plan)
 {

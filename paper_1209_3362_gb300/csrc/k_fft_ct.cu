@@ -1,11 +1,15 @@
-// Compile-time-specialised FP32 FFT passes for the common frame sizes (same transforms as the
+// Compile-time-specialised FP32 FFT passes for the common frame sizes (the same transforms as the
 // generic kernels in k_fft.cu: unscaled forward DFT, rows as half-length complex transforms plus
-// the real-to-complex split, then columns in place; tile-major ring).
+// the real-to-complex split, then columns).
 //
 // With the transform length, radices and batch known at compile time every index is a shift or
-// a constant multiply, every per-thread loop unrolls, and each thread keeps several butterflies'
-// inputs in registers.  The column pass runs in place in one shared buffer (all butterfly inputs
-// of a stage are read into registers before any output is written), so three CTAs fit per SM.
+// a constant multiply and every per-thread loop unrolls.  Twiddles come from a per-stage table in
+// which consecutive butterflies read consecutive entries; shared memory is padded by one element
+// in 16 so the strided stores of the early Stockham stages do not collide in banks.  The row pass
+// writes the column-pair scratch, which the column pass reads as one contiguous run per CTA; the
+// column pass (in place in one buffer) writes each column as whole 32-mode tile rows of the ring.
+#include <cmath>
+
 #include "nfs_internal.cuh"
 
 namespace nfs {
@@ -62,9 +66,9 @@ struct Dft<8> {
         Dft<4>::run(e);
         Dft<4>::run(o);
         const float h = 0.70710678118654752440f;
-        const float2 o1 = {h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};    // (1 - i)/sqrt2 * o1
-        const float2 o2 = cmi(o[2]);                                          // -i * o2
-        const float2 o3 = {h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};   // (-1 - i)/sqrt2 * o3
+        const float2 o1 = {h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};   // (1 - i)/sqrt2 * o1
+        const float2 o2 = cmi(o[2]);                                         // -i * o2
+        const float2 o3 = {h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};  // (-1 - i)/sqrt2 * o3
         v[0] = cadd(e[0], o[0]);
         v[4] = csub(e[0], o[0]);
         v[1] = cadd(e[1], o1);
@@ -76,20 +80,33 @@ struct Dft<8> {
     }
 };
 
-template <int REM>
-struct Pick {
-    static constexpr int R = (REM % 8 == 0 && REM != 16) ? 8 : (REM % 4 == 0 ? 4 : (REM % 2 == 0 ? 2 : 3));
-};
+// Radix of the next stage given the remaining length (also used on the host for the tables).
+__host__ __device__ constexpr int pick_radix(int rem)
+{
+    return (rem % 8 == 0 && rem != 16) ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3));
+}
+// Offset of the stage with sub-length NS in the per-stage twiddle table of length L.
+__host__ __device__ constexpr int tw_offset(int L, int NS)
+{
+    int off = 0, ns = 1;
+    while (ns < NS) {
+        const int r = pick_radix(L / ns);
+        off += ns * (r - 1);
+        ns *= r;
+    }
+    return off;
+}
+__host__ __device__ constexpr int padded(int x) { return x + (x >> 4); }
 
 // One Stockham stage on NB transforms of length L (element (b, i) at b*L + i, or i*NB + b when
-// BFAST), NT threads.  INPLACE: in == out, all inputs are read before a barrier, then written.
+// BFAST; padded), NT threads.  INPLACE: in == out, all inputs are read before a barrier.
 template <int L, int R, int NS, int NB, bool BFAST, bool INPLACE, int NT>
-__device__ __forceinline__ void stage(const float2 *in, float2 *out, const float2 *__restrict__ tw)
+__device__ __forceinline__ void stage(const float2 *in, float2 *out, const float2 *__restrict__ tws)
 {
     constexpr int NBF = L / R;
     constexpr int TOT = NB * NBF;
     constexpr int PER = (TOT + NT - 1) / NT;
-    constexpr int TWS = L / (NS * R);
+    constexpr int OFF = tw_offset(L, NS);
     float2 v[PER][R];
     int jj[PER], bb[PER];
 #pragma unroll
@@ -109,7 +126,7 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int i = j + r * NBF;
-                v[p][r] = in[BFAST ? i * NB + b : b * L + i];
+                v[p][r] = in[padded(BFAST ? i * NB + b : b * L + i)];
             }
         }
     }
@@ -122,32 +139,32 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
             const int k = j % NS;
             if (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tw + k * r * TWS));
+                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tws + OFF + k * (R - 1) + (r - 1)));
             }
             Dft<R>::run(v[p]);
             const int base = (j / NS) * NS * R + k;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 const int i = base + r * NS;
-                out[BFAST ? i * NB + b : b * L + i] = v[p][r];
+                out[padded(BFAST ? i * NB + b : b * L + i)] = v[p][r];
             }
         }
     }
 }
 
 template <int L, int NS, int NB, bool BFAST, bool INPLACE, int NT>
-__device__ __forceinline__ float2 *run_stages(float2 *a, float2 *b, const float2 *__restrict__ tw)
+__device__ __forceinline__ float2 *run_stages(float2 *a, float2 *b, const float2 *__restrict__ tws)
 {
     if constexpr (NS >= L) {
         return a;
     } else {
-        constexpr int R = Pick<L / NS>::R;
-        stage<L, R, NS, NB, BFAST, INPLACE, NT>(a, INPLACE ? a : b, tw);
+        constexpr int R = pick_radix(L / NS);
+        stage<L, R, NS, NB, BFAST, INPLACE, NT>(a, INPLACE ? a : b, tws);
         __syncthreads();
         if constexpr (INPLACE)
-            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(a, b, tw);
+            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(a, b, tws);
         else
-            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(b, a, tw);
+            return run_stages<L, NS * R, NB, BFAST, INPLACE, NT>(b, a, tws);
     }
 }
 
@@ -162,20 +179,21 @@ __host__ __device__ constexpr int rows_per_cta(int L)
     return r;
 }
 
-// Row pass for frames of width W = 2L: RPC rows per CTA, 8 complex points per thread.
+// Row pass for frames of width W = 2L: RPC rows per CTA, 8 complex points per thread; output to
+// the column-pair scratch of frame blockIdx.y.
 template <int L>
 __global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__ frames,
                                                     const unsigned long long *__restrict__ sums,
                                                     const float *__restrict__ ref, Geometry g,
-                                                    const float2 *__restrict__ tw, const float2 *__restrict__ twp,
-                                                    float2 *__restrict__ ring, int R, int slot0)
+                                                    const float2 *__restrict__ tws, const float2 *__restrict__ twp,
+                                                    float2 *__restrict__ scratch)
 {
     constexpr int RPC = rows_per_cta(L);
     constexpr int N = RPC * L;
     constexpr int PER = N / kNT;
     static_assert(N % kNT == 0, "row batch must fill the CTA");
-    __shared__ __align__(16) float2 bufA[N];
-    __shared__ __align__(16) float2 bufB[N];
+    __shared__ __align__(16) float2 bufA[padded(N)];
+    __shared__ __align__(16) float2 bufB[padded(N)];
     const int f = blockIdx.y;
     const int row0 = blockIdx.x * RPC;
     const unsigned long long S = sums[f];
@@ -205,134 +223,152 @@ __global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__
     for (int p = 0; p < PER; ++p) {
         const int e = threadIdx.x + p * kNT;
         const float a = (float)(raw[p] & 0xffffu), b = (float)(raw[p] >> 16);
-        bufA[e] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -rf[p].x)),
-                   __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -rf[p].y))};
+        bufA[padded(e)] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -rf[p].x)),
+                           __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -rf[p].y))};
     }
     __syncthreads();
-    const float2 *Z = run_stages<L, 1, RPC, false, false, kNT>(bufA, bufB, tw);
+    const float2 *Z = run_stages<L, 1, RPC, false, false, kNT>(bufA, bufB, tws);
 
-    const int slot = (slot0 + f) % R;
+    // outputs k < WP of each row, laid out so that a thread group covers the RPC rows of one
+    // column pair (contiguous in the scratch)
     constexpr int WP = ((L + 1) + 3) / 4 * 4;
+    float2 *out = scratch + (size_t)f * g.H * WP;
     for (int e = threadIdx.x; e < RPC * WP; e += kNT) {
-        const int r = e / WP, k = e % WP;
+        const int c = e & 1, r = (e >> 1) % RPC, kp = (e >> 1) / RPC;
+        const int k = 2 * kp + c;
         const int y = row0 + r;
         if (y >= g.H) continue;
         float2 X = {0.f, 0.f};
         if (k <= L) {
-            const float2 zk = Z[r * L + (k == L ? 0 : k)];
-            float2 zc = Z[r * L + (k == 0 ? 0 : L - k)];
+            const float2 zk = Z[padded(r * L + (k == L ? 0 : k))];
+            float2 zc = Z[padded(r * L + (k == 0 ? 0 : L - k))];
             zc.y = -zc.y;
             const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
             const float2 d = csub(zk, zc);
             const float2 O = {0.5f * d.y, -0.5f * d.x};
             X = cadd(E, cmul(__ldg(twp + k), O));
         }
-        ring[ring_index(slot, (size_t)y * WP + k, R)] = X;
+        out[((size_t)kp * g.H + y) * 2 + c] = X;
     }
 }
 
-// Columns per CTA of the column pass: 4, or 2 at H = 2048 (keeps the butterflies in registers).
-__host__ __device__ constexpr int cols_per_cta(int H) { return H >= 2048 ? 2 : 4; }
-
-// Column pass for frames of height H: CB adjacent columns per CTA, in place.
-template <int H>
-__global__ void __launch_bounds__(kNT, 2) k_col_fft_ct(Geometry g, const float2 *__restrict__ tw,
-                                                    float2 *__restrict__ ring, int R, int slot0)
+// Threads of the column pass: the largest of 256, 128, 64 that divides the 2H points of a pair.
+__host__ __device__ constexpr int col_threads(int H)
 {
-    constexpr int CB = cols_per_cta(H);
-    constexpr int N = H * CB;
-    constexpr int PER = N / kNT;
-    static_assert(N % kNT == 0, "column batch must fill the CTA");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    float2 *buf = reinterpret_cast<float2 *>(smem_raw);
+    return (2 * H) % 256 == 0 ? 256 : ((2 * H) % 128 == 0 ? 128 : 64);
+}
+
+// Column pass for frames of height H: one column pair per CTA, read contiguously from the scratch,
+// transformed in place, written as whole tile rows of the ring (column-major modes).
+template <int H>
+__global__ void __launch_bounds__(col_threads(H)) k_col_fft_ct(Geometry g, const float2 *__restrict__ tws,
+                                                               const float2 *__restrict__ scratch,
+                                                               float2 *__restrict__ ring, int R, int slot0)
+{
+    constexpr int NT = col_threads(H);
+    constexpr int N = H * 2;
+    constexpr int PER = N / NT;
+    static_assert(N % NT == 0, "column batch must fill the CTA");
+    __shared__ __align__(16) float2 buf[padded(N)];
     const int f = blockIdx.y;
-    const int x0 = blockIdx.x * CB;
+    const int kp = blockIdx.x;
     const int slot = (slot0 + f) % R;
-    constexpr int CH = PER % 8 == 0 ? 8 : (PER % 6 == 0 ? 6 : (PER % 4 == 0 ? 4 : PER));  // loads in flight per thread
-    static_assert(PER % CH == 0, "chunked loads");
-#pragma unroll
-    for (int p0 = 0; p0 < PER; p0 += CH) {
-        float2 v[CH];
-#pragma unroll
-        for (int q = 0; q < CH; ++q) {
-            const int e = threadIdx.x + (p0 + q) * kNT;
-            const int y = e / CB, c = e % CB;
-            v[q] = ring[ring_index(slot, (size_t)y * g.Wp + x0 + c, R)];
-        }
-#pragma unroll
-        for (int q = 0; q < CH; ++q) buf[threadIdx.x + (p0 + q) * kNT] = v[q];
-    }
-    __syncthreads();
-    const float2 *Y = run_stages<H, 1, CB, true, true, kNT>(buf, buf, tw);
+    const float2 *src = scratch + (size_t)f * H * g.Wp + (size_t)kp * H * 2;
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-        const int e = threadIdx.x + p * kNT;
-        const int y = e / CB, c = e % CB;
-        ring[ring_index(slot, (size_t)y * g.Wp + x0 + c, R)] = Y[e];
+        const int e = threadIdx.x + p * NT;
+        buf[padded(e)] = __ldg(src + e);  // e = y * 2 + c: the BFAST layout of two columns
+    }
+    __syncthreads();
+    const float2 *Y = run_stages<H, 1, 2, true, true, NT>(buf, buf, tws);
+#pragma unroll
+    for (int p = 0; p < PER; ++p) {
+        const int e = threadIdx.x + p * NT;
+        const int c = e / H, y = e % H;
+        const int kx = 2 * kp + c;
+        if (kx < g.Wh) ring[ring_index(slot, (size_t)kx * H + y, R)] = Y[padded(y * 2 + c)];
     }
 }
 
 }  // namespace ct
 
+std::vector<double> ct_stage_twiddles(int L)
+{
+    std::vector<double> t;
+    int ns = 1;
+    while (ns < L) {
+        const int r = ct::pick_radix(L / ns);
+        for (int k = 0; k < ns; ++k)
+            for (int q = 1; q < r; ++q) {
+                const double a = 2.0 * M_PI * (double)k * q / ((double)ns * r);
+                t.push_back(std::cos(a));
+                t.push_back(-std::sin(a));
+            }
+        ns *= r;
+    }
+    return t;
+}
+
 template <int L>
 static cudaError_t row_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
-                          const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
-                          cudaStream_t s)
+                          const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch, cudaStream_t s)
 {
     constexpr int RPC = ct::rows_per_cta(L);
     dim3 grid((g.H + RPC - 1) / RPC, nf);
-    ct::k_row_fft_ct<L><<<grid, ct::kNT, 0, s>>>(frames, sums, ref, g, tw, twp, ring, R, slot0);
+    ct::k_row_fft_ct<L><<<grid, ct::kNT, 0, s>>>(frames, sums, ref, g, tws, twp, scratch);
     return cudaGetLastError();
 }
 
 template <int H>
-static cudaError_t col_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0, cudaStream_t s)
+static cudaError_t col_ct(int nf, const Geometry &g, const float2 *tws, const float2 *scratch, float2 *ring, int R,
+                          int slot0, cudaStream_t s)
 {
-    constexpr int CB = ct::cols_per_cta(H);
-    const size_t smem = (size_t)H * CB * sizeof(float2);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(ct::k_col_fft_ct<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    dim3 grid(g.Wp / CB, nf);
-    ct::k_col_fft_ct<H><<<grid, ct::kNT, smem, s>>>(g, tw, ring, R, slot0);
+    dim3 grid(g.Wp / 2, nf);
+    ct::k_col_fft_ct<H><<<grid, ct::col_threads(H), 0, s>>>(g, tws, scratch, ring, R, slot0);
     return cudaGetLastError();
 }
 
-// Returns cudaErrorNotSupported when no specialised kernel exists for the size (the caller then
-// uses the generic kernel).
-cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
-                              const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
-                              cudaStream_t s)
+static bool ct_size(int n)
 {
-    if ((reinterpret_cast<uintptr_t>(frames) & 3) || g.Wp != ((g.Lr + 1) + 3) / 4 * 4) return cudaErrorNotSupported;
+    switch (n) {
+        case 64: case 128: case 192: case 256: case 384: case 512: case 768: case 1024: case 2048: return true;
+        default: return false;
+    }
+}
+
+cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
+                              const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch, cudaStream_t s)
+{
+    if (!tws || (reinterpret_cast<uintptr_t>(frames) & 3) || g.Wp != ((g.Lr + 1) + 3) / 4 * 4 || !ct_size(g.Lr))
+        return cudaErrorNotSupported;
     switch (g.Lr) {
-        case 64: return row_ct<64>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 128: return row_ct<128>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 192: return row_ct<192>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 256: return row_ct<256>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 384: return row_ct<384>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 512: return row_ct<512>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 768: return row_ct<768>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 1024: return row_ct<1024>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
-        case 2048: return row_ct<2048>(frames, nf, sums, ref, g, tw, twp, ring, R, slot0, s);
+        case 64: return row_ct<64>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 128: return row_ct<128>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 192: return row_ct<192>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 256: return row_ct<256>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 384: return row_ct<384>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 512: return row_ct<512>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 768: return row_ct<768>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 1024: return row_ct<1024>(frames, nf, sums, ref, g, tws, twp, scratch, s);
+        case 2048: return row_ct<2048>(frames, nf, sums, ref, g, tws, twp, scratch, s);
         default: return cudaErrorNotSupported;
     }
 }
 
-cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0,
-                              cudaStream_t s)
+cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tws, const float2 *scratch, float2 *ring,
+                              int R, int slot0, cudaStream_t s)
 {
-    if (g.Wp % 4) return cudaErrorNotSupported;
+    if (!tws || !g.colmajor || !ct_size(g.H)) return cudaErrorNotSupported;
     switch (g.H) {
-        case 64: return col_ct<64>(nf, g, tw, ring, R, slot0, s);
-        case 128: return col_ct<128>(nf, g, tw, ring, R, slot0, s);
-        case 256: return col_ct<256>(nf, g, tw, ring, R, slot0, s);
-        case 384: return col_ct<384>(nf, g, tw, ring, R, slot0, s);
-        case 512: return col_ct<512>(nf, g, tw, ring, R, slot0, s);
-        case 768: return col_ct<768>(nf, g, tw, ring, R, slot0, s);
-        case 1024: return col_ct<1024>(nf, g, tw, ring, R, slot0, s);
-        case 2048: return col_ct<2048>(nf, g, tw, ring, R, slot0, s);
+        case 64: return col_ct<64>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 128: return col_ct<128>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 192: return col_ct<192>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 256: return col_ct<256>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 384: return col_ct<384>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 512: return col_ct<512>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 768: return col_ct<768>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 1024: return col_ct<1024>(nf, g, tws, scratch, ring, R, slot0, s);
+        case 2048: return col_ct<2048>(nf, g, tws, scratch, ring, R, slot0, s);
         default: return cudaErrorNotSupported;
     }
 }

@@ -15,7 +15,8 @@ namespace {
 
 constexpr int kDefaultBlock = kDelayBlock;  // K: frames per fused delay update
 constexpr int kMaxBlock = kDelayBlock;      // largest K the fused kernel takes
-constexpr int kMaxChunk = 64;       // largest FFT chunk
+constexpr int kMaxChunk = 64;       // largest FFT chunk (FP64 path)
+constexpr int kMaxChunkF32 = 16;    // largest FFT chunk of the FP32 path (its scratch holds 16 frames)
 constexpr int kMaxDim = 4096;
 constexpr int kMaxDelay = 65536;
 
@@ -77,6 +78,8 @@ struct nfs_ctx {
     void *d_acc = nullptr;
     int *d_delays = nullptr;
     void *d_tw_row = nullptr, *d_tw_post = nullptr, *d_tw_col = nullptr;
+    float2 *d_tws_row = nullptr, *d_tws_col = nullptr;  // per-stage twiddles of the specialised FFTs
+    float2 *d_scratch = nullptr;                         // FP32 row-pass output, kMaxChunkF32 frames
     FftPlan plan_row, plan_col;
     int *d_bin_off = nullptr, *d_bin_modes = nullptr;
     long long *d_pairs = nullptr, *d_counts = nullptr;
@@ -202,6 +205,17 @@ int upload_post(nfs_ctx *c, int W, void **dst)
     return NFS_OK;
 }
 
+// Per-stage twiddles of the size-specialised FP32 kernels (FP64 on the host, rounded once).
+int upload_stage_twiddles(nfs_ctx *c, int L, float2 **dst)
+{
+    const std::vector<double> t = ct_stage_twiddles(L);
+    std::vector<float2> h(std::max<size_t>(t.size() / 2, 1));
+    for (size_t i = 0; i < t.size() / 2; ++i) h[i] = {(float)t[2 * i], (float)t[2 * i + 1]};
+    CK(c, cudaMalloc((void **)dst, sizeof(float2) * h.size()));
+    CK(c, cudaMemcpy(*dst, h.data(), sizeof(float2) * h.size(), cudaMemcpyHostToDevice));
+    return NFS_OK;
+}
+
 // Radial bin of every half-plane mode (integer rule of the header), as a CSR list by bin.
 int build_bins(nfs_ctx *c)
 {
@@ -220,7 +234,7 @@ int build_bins(nfs_ctx *c)
                                          (unsigned long long)L;
             if (b >= (unsigned long long)nq) continue;
             const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
-            const long long idx = (long long)ky * c->g.Wp + kx;
+            const long long idx = (long long)c->g.mode(kx, ky);
             lists[b].push_back((int)((idx << 1) | two));
             c->counts[b] += two ? 2 : 1;
             qsum[b] += (two ? 2.0 : 1.0) * 2.0 * M_PI * std::sqrt((double)r2) / (double)L;
@@ -270,6 +284,9 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_tw_row);
     cudaFree(c->d_tw_post);
     cudaFree(c->d_tw_col);
+    cudaFree(c->d_tws_row);
+    cudaFree(c->d_tws_col);
+    cudaFree(c->d_scratch);
     cudaFree(c->d_bin_off);
     cudaFree(c->d_bin_modes);
     cudaFree(c->d_pairs);
@@ -334,12 +351,12 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
         rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
             return launch_row_fft<float>(dsrc, nf, c->d_sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
                                          (const float2 *)c->d_tw_post, (float2 *)c->d_ring, c->R, slot0, c->stream,
-                                         c->fft_generic != 0);
+                                         c->d_scratch, c->fft_generic ? nullptr : c->d_tws_row);
         }, "row_fft_f32");
         if (rc) return rc;
         rc = timed(c, NFS_STAGE_COLFFT, c->stream, [&] {
             return launch_col_fft<float>(nf, c->g, c->plan_col, (const float2 *)c->d_tw_col, (float2 *)c->d_ring, c->R,
-                                         slot0, c->stream, c->fft_generic != 0);
+                                         slot0, c->stream, c->d_scratch, c->fft_generic ? nullptr : c->d_tws_col);
         }, "col_fft_f32");
         if (rc) return rc;
         c->nframes += nf;
@@ -409,15 +426,10 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     c->nq = n_qbins;
     c->delays.assign(delays, delays + n_delays);
     c->tau_max = delays[n_delays - 1];
-    c->g.H = H;
-    c->g.W = W;
-    c->g.Lr = W / 2;
-    c->g.Wh = W / 2 + 1;
-    c->g.Wp = (c->g.Wh + 3) / 4 * 4;
-    c->g.M = ((size_t)H * c->g.Wp + kTile - 1) / kTile * kTile;
-    c->g.HW = (size_t)H * W;
+    c->g = make_geometry(H, W, c->f32());
     c->R = c->tau_max + (c->f32() ? c->K : kMaxChunk);
-    c->stage_frames = (int)std::max<size_t>(1, std::min<size_t>(kMaxChunk, (64u << 20) / c->frame_bytes()));
+    c->stage_frames = (int)std::max<size_t>(
+        1, std::min<size_t>(c->f32() ? kMaxChunkF32 : kMaxChunk, (64u << 20) / c->frame_bytes()));
     c->fft_chunk = std::min(4, c->stage_frames);
     c->pairs_h.assign((size_t)n_delays, 0);
 
@@ -452,8 +464,11 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     if (cudaMemset(c->d_acc, 0, acc_bytes) != cudaSuccess) return bail(NFS_ECUDA);
     if (c->f32()) {
         if (upload_twiddles<float>(c, c->g.Lr, &c->d_tw_row) || upload_twiddles<float>(c, H, &c->d_tw_col) ||
-            upload_post<float>(c, W, &c->d_tw_post))
+            upload_post<float>(c, W, &c->d_tw_post) || upload_stage_twiddles(c, c->g.Lr, &c->d_tws_row) ||
+            upload_stage_twiddles(c, H, &c->d_tws_col))
             return bail(NFS_ECUDA);
+        if ((rc = alloc_dev(c, (void **)&c->d_scratch, sizeof(float2) * (size_t)kMaxChunkF32 * H * c->g.Wp)))
+            return bail(rc);
     } else {
         if (upload_twiddles<double>(c, c->g.Lr, &c->d_tw_row) || upload_twiddles<double>(c, H, &c->d_tw_col) ||
             upload_post<double>(c, W, &c->d_tw_post))
@@ -678,7 +693,7 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
     switch (key) {
         case NFS_OPT_TIMING: c->timing = v != 0; return NFS_OK;
         case NFS_OPT_FFT_CHUNK:
-            if (v < 1 || v > kMaxChunk) return NFS_EINVAL;
+            if (v < 1 || v > (c->f32() ? kMaxChunkF32 : kMaxChunk)) return NFS_EINVAL;
             c->fft_chunk = (int)v;
             return NFS_OK;
         case NFS_OPT_DELAY_VARIANT:

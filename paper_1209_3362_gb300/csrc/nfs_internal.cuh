@@ -34,14 +34,30 @@ struct FftPlan {
 bool make_plan(int L, FftPlan *plan);  // false if L has a prime factor other than 2 or 3
 
 // One device-side description of the frame geometry.
+//
+// Mode order of a spectrum in HBM (the flat index k the delay update and the binning use):
+//   column-major (FP32 path):  k = kx * H + ky,  kx < W/2+1, ky < H   (M = H (W/2+1) rounded up to 32)
+//   row-major    (FP64 path):  k = ky * Wp + kx, kx < Wp (pitch)      (M = H Wp rounded up to 32)
+// The FP32 row pass writes a column-pair scratch [kx/2][ky][kx%2] (Wp columns) that the column
+// pass reads as contiguous runs of 2 columns.
 struct Geometry {
     int H, W;      // frame size
     int Lr;        // row transform length W/2
     int Wh;        // W/2 + 1 non-redundant columns
-    int Wp;        // row pitch of spectra in HBM (complex values), Wp >= Wh, multiple of 4
-    size_t M;      // complex values per spectrum: H * Wp rounded up to a multiple of 32
+    int Wp;        // W/2 + 1 rounded up to a multiple of 4 (row pitch / scratch columns)
+    size_t M;      // complex values per spectrum (multiple of 32)
     size_t HW;     // pixels per frame
+    int colmajor;  // 1: column-major mode order (FP32), 0: row-major with pitch Wp (FP64)
+    __host__ __device__ size_t mode(int kx, int ky) const
+    {
+        return colmajor ? (size_t)kx * H + ky : (size_t)ky * Wp + kx;
+    }
+    __host__ __device__ size_t scratch_index(int kx, int ky) const  // FP32 column-pair scratch
+    {
+        return ((size_t)(kx >> 1) * H + ky) * 2 + (kx & 1);
+    }
 };
+Geometry make_geometry(int H, int W, bool colmajor);
 
 // --------------------------------------------------------------- launchers (stream-ordered)
 
@@ -53,25 +69,34 @@ cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g,
 cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
                              float *ref, cudaStream_t s);
 
-// Row pass: for nf frames, normalise (and subtract ref when T = float) and write the r2c row
-// transforms [H][Wp] into ring slots (slot0 + f) % R (tile-major for float, slot-major for double).
+// Row pass: for nf frames, normalise (and subtract ref when T = float) and transform every row.
+// FP32: writes the column-group scratch of frame f at scratch + f * H * Wp.  FP64: writes the
+// row transforms [H][Wp] into ring slot (slot0 + f) % R (slot-major ring).
+// tws_row: per-stage twiddles of the size-specialised FP32 kernels (NULL: generic kernels only).
 template <typename T>
 cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                            const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_row,
                            const typename cplx_t<T>::type *tw_post, typename cplx_t<T>::type *ring, int R,
-                           int slot0, cudaStream_t s, bool generic_only = false);
+                           int slot0, cudaStream_t s, typename cplx_t<T>::type *scratch = nullptr,
+                           const float2 *tws_row = nullptr);
 
-// Compile-time-specialised FP32 passes (tile-major ring); cudaErrorNotSupported for sizes without one.
+// Compile-time-specialised FP32 passes; cudaErrorNotSupported for sizes without one.
 cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
-                              const Geometry &g, const float2 *tw, const float2 *twp, float2 *ring, int R, int slot0,
+                              const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch,
                               cudaStream_t s);
-cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tw, float2 *ring, int R, int slot0,
-                              cudaStream_t s);
+cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tws, const float2 *scratch, float2 *ring,
+                              int R, int slot0, cudaStream_t s);
+// Per-stage twiddle table of the specialised kernels for length L (stage s with sub-length NS and
+// radix R holds exp(-2 pi i k r / (NS R)) at offset(s) + k (R - 1) + r - 1); empty if none.
+std::vector<double> ct_stage_twiddles(int L);
 
-// Column pass: in-place length-H transforms of the nf ring slots written by the row pass.
+// Column pass: length-H transforms of the nf frames of the row pass.  FP32: reads the scratch,
+// writes ring slots (slot0 + f) % R (tile-major ring, column-major modes).  FP64: in place in the
+// slot-major ring.
 template <typename T>
 cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const typename cplx_t<T>::type *tw_col,
-                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s, bool generic_only = false);
+                           typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s,
+                           const typename cplx_t<T>::type *scratch = nullptr, const float2 *tws_col = nullptr);
 
 // Layout of the FP32 spectrum ring: tiles of 32 consecutive modes (flat k = ky * Wp + kx), each
 // tile holding its R slots contiguously, [tile][slot][32] float2, so the time series of a tile is

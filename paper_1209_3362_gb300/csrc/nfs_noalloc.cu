@@ -66,13 +66,15 @@ __device__ unsigned long long na_isqrt(unsigned long long v)
     return r;
 }
 
-// bin_of[ky * Wp + kx] = (bin << 1) | (weight == 2), or -1 for excluded and padding modes.
+// bin_of[mode(kx, ky)] = (bin << 1) | (weight == 2), or -1 for excluded modes (padding modes are
+// set to -1 beforehand).
 __global__ void k_na_bin_index(int *bin_of, Geometry g, int nq, long long L)
 {
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < g.M; i += (size_t)gridDim.x * blockDim.x) {
-        const int ky = (int)(i / g.Wp), kx = (int)(i - (size_t)ky * g.Wp);
+    const size_t n = (size_t)g.H * g.Wh;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const int ky = (int)(i / g.Wh), kx = (int)(i - (size_t)ky * g.Wh);
         int code = -1;
-        if (kx < g.Wh && !(kx == 0 && ky == 0)) {
+        if (!(kx == 0 && ky == 0)) {
             const long long kys = (ky <= g.H / 2) ? ky : ky - g.H;
             const long long m = (long long)kx * (L / g.W), n = kys * (L / g.H);
             const unsigned long long r2 = (unsigned long long)(m * m + n * n);
@@ -80,7 +82,7 @@ __global__ void k_na_bin_index(int *bin_of, Geometry g, int nq, long long L)
                 na_isqrt(4ull * (unsigned long long)nq * (unsigned long long)nq * r2) / (unsigned long long)L;
             if (b < (unsigned long long)nq) code = (int)(b << 1) | ((kx != 0 && kx != g.W / 2) ? 1 : 0);
         }
-        bin_of[i] = code;
+        bin_of[g.mode(kx, ky)] = code;
     }
 }
 
@@ -168,14 +170,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     if (H < 2 || W < 2 || H > 4096 || W > 4096 || (H % 2) || (W % 2) || !factors_2_3_na(H) || !factors_2_3_na(W / 2))
         return NFS_EUNSUPPORTED;
 
-    Geometry g;
-    g.H = H;
-    g.W = W;
-    g.Lr = W / 2;
-    g.Wh = W / 2 + 1;
-    g.Wp = (g.Wh + 3) / 4 * 4;
-    g.M = ((size_t)H * g.Wp + kTile - 1) / kTile * kTile;
-    g.HW = (size_t)H * W;
+    const Geometry g = make_geometry(H, W, true);
     FftPlan prow, pcol;
     if (!make_plan(g.Lr, &prow) || !make_plan(H, &pcol)) return NFS_EUNSUPPORTED;
     const int nd = n_delays, nq = n_qbins;
@@ -187,6 +182,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     const size_t o_acc = carve(&off, (size_t)nd * g.M * sizeof(float2));
     const size_t o_sums = carve(&off, sizeof(unsigned long long) * kNaChunk);
     const size_t o_ref = carve(&off, sizeof(float) * g.HW);
+    const size_t o_scr = carve(&off, sizeof(float2) * (size_t)kNaChunk * H * g.Wp);
     const size_t o_twr = carve(&off, sizeof(float2) * (size_t)(g.Lr > 0 ? g.Lr : 1));
     const size_t o_twc = carve(&off, sizeof(float2) * (size_t)H);
     const size_t o_twp = carve(&off, sizeof(float2) * (size_t)g.Wh);
@@ -205,6 +201,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     float2 *acc = (float2 *)(base + o_acc);
     unsigned long long *sums = (unsigned long long *)(base + o_sums);
     float *ref = (float *)(base + o_ref);
+    float2 *scr = (float2 *)(base + o_scr);
     float2 *twr = (float2 *)(base + o_twr), *twc = (float2 *)(base + o_twc), *twp = (float2 *)(base + o_twp);
     int *bin_of = (int *)(base + o_bin);
     long long *cnt = (long long *)(base + o_cnt), *pairs = (long long *)(base + o_pairs);
@@ -221,6 +218,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     k_na_twiddles<float2><<<8, 256, 0, s>>>(twc, H, H);
     k_na_twiddles<float2><<<8, 256, 0, s>>>(twp, W, g.Wh);
     const long long L = (long long)H / gcd_na(H, W) * W;
+    NA_CK(cudaMemsetAsync(bin_of, 0xff, sizeof(int) * g.M, s));
     k_na_bin_index<<<256, 256, 0, s>>>(bin_of, g, nq, L);
     k_na_bin_counts<<<256, 256, 0, s>>>(bin_of, g.M, cnt);
     NA_CK(cudaGetLastError());
@@ -234,8 +232,8 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
         NA_CK(launch_frame_sums(src, nf, g, sums, s));
         if (done == 0) NA_CK(launch_reference(src, sums, g, ref, s));
         const int slot0 = (int)(done % R);
-        NA_CK(launch_row_fft<float>(src, nf, sums, ref, g, prow, twr, twp, ring, R, slot0, s));
-        NA_CK(launch_col_fft<float>(nf, g, pcol, twc, ring, R, slot0, s));
+        NA_CK(launch_row_fft<float>(src, nf, sums, ref, g, prow, twr, twp, ring, R, slot0, s, scr, nullptr));
+        NA_CK(launch_col_fft<float>(nf, g, pcol, twc, ring, R, slot0, s, scr, nullptr));
         done += nf;
         if (done - processed == kNaBlock || done == n_frames) {
             DelayArgs a{ring, R, g.M, processed, (int)(done - processed), dd, nd, acc, nullptr, nullptr, delays[nd - 1]};
