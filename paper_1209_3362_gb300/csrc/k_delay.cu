@@ -19,6 +19,7 @@
 // computes when both fit.  Per-warp partial sums go through shared memory, are added in a fixed
 // warp order and then into the Kahan (sum, compensation) pair of the accumulator.
 #include <algorithm>
+#include <cmath>
 
 #include "nfs_internal.cuh"
 
@@ -50,8 +51,9 @@ bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, s
         j = j0 + len;
     }
     const int K = kDelayBlock, SB = kSlotBuf, SPAN = 64;
-    int lo_prev = 0;     // frames t0 + lo_prev .. are in the buffer after the new block is loaded
-    int dmin_prev = 0;   // the new block itself is the "previous" range of stage 0
+    // needed frame range of every consumer step, relative to t0: step 0 reads the block itself
+    std::vector<int> need_lo(1, 0), need_hi(1, K - 1);
+    int lo_prev = 0;  // frames t0 + lo_prev .. are in the buffer after the block is loaded
     size_t r = 0;
     while (r < srs->size()) {
         Stage st;
@@ -69,11 +71,36 @@ bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, s
         st.lo = -dmax;
         st.hi = std::min(lo_prev - 1, K - 1 - dmin);
         if (K + dmax - dmin > SB) return false;  // cannot happen with SPAN = 64
-        st.prefetch = (sts->empty() ? 0 : (K + dmax - dmin_prev <= SB)) ? 1 : 0;
         if (st.lo <= st.hi) lo_prev = st.lo;
-        dmin_prev = dmin;
+        need_lo.push_back(-dmax);
+        need_hi.push_back(K - 1 - dmin);
         sts->push_back(st);
         r = e;
+    }
+    // When may the group of stage s (group g = s + 1, consumed by step g) be issued?  Its rows of the
+    // slot ring must no longer hold frames a pending step reads (a frame f sits in row f mod SB), and
+    // the mbarrier it reuses (group g - kFullBars, consumed by step g - kFullBars) must have been
+    // observed by every consumer.
+    for (size_t s = 0; s < sts->size(); ++s) {
+        Stage &st = (*sts)[s];
+        const int g = (int)s + 1;
+        int need = std::max(0, g - kFullBars + 1);
+        if (st.lo <= st.hi) {
+            for (int q = g - 1; q >= 0; --q) {  // latest earlier step that reads a row the group overwrites
+                // frames f in [lo, hi] and h in [need_lo, need_hi] share a row iff h = f + k SB, k != 0
+                bool clash = false;
+                const int a = st.lo, b = st.hi, c = need_lo[q], d = need_hi[q];
+                const int kmin = (int)std::floor((double)(c - b) / SB), kmax = (int)std::ceil((double)(d - a) / SB);
+                for (int k = kmin; k <= kmax && !clash; ++k)
+                    if (k != 0 && std::max(a, c - k * SB) <= std::min(b, d - k * SB)) clash = true;
+                if (clash) {
+                    need = std::max(need, q + 1);
+                    break;
+                }
+            }
+        }
+        if (need > g) return false;  // the step that needs this group would wait for itself
+        st.need = need;
     }
     return true;
 }
@@ -122,21 +149,11 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
-// Waits for the phase of a copy group; gives up after limit_ns (returns false).
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity,
-                                                  unsigned long long limit_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > limit_ns) return false;
-    return true;
-}
-
 // ------------------------------------------------------------------ tiled kernel
 
-constexpr int kWarps = 16;  // warps per CTA
-constexpr int kTw = 16;     // consecutive frames per warp
+constexpr int kWarps = 16;                       // consumer warps (16 frames each)
+constexpr int kTw = 16;                          // consecutive frames per consumer warp
+constexpr int kThreads = (kWarps + 1) * 32;      // + one producer warp that issues the copies
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 static_assert(kWarps * kTw == kDelayBlock, "block = warps x frames per warp");
 
@@ -144,10 +161,36 @@ struct TiledSmem {
     float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf
     float red[16][kWarps][kTile];          // per-warp partial sums of up to 16 pending delays
     int jd[16];                            // delay indices of the pending partials
-    unsigned long long bar[2];             // copy-group barriers
+    unsigned long long full[kFullBars];    // copy-group barriers (group g on full[g % kFullBars])
+    int done;                              // consumer-warp step completions (kWarps per step)
+    int abort;                             // set when a bounded wait gives up
 };
 
-// Issue the bulk copies of frames t0+lo .. t0+hi of this tile into the slot ring (thread 0 only).
+__device__ __forceinline__ void set_abort(TiledSmem &S, int *err)
+{
+    *(volatile int *)&S.abort = 1;
+    atomicExch(err, 1);
+}
+
+// Wait for copy group g (bounded; returns at once once any thread of the CTA has given up).
+__device__ __forceinline__ bool wait_group(TiledSmem &S, int g, int *err)
+{
+    unsigned long long *bar = &S.full[g % kFullBars];
+    const unsigned par = (unsigned)((g / kFullBars) & 1);
+    if (mbar_try_wait(bar, par)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, par)) {
+        // give up at once when this CTA or any other CTA of the launch has given up
+        if (*(volatile int *)&S.abort || *(volatile int *)err) return false;
+        if (global_ns() - t0 > kWaitLimitNs) {
+            set_abort(S, err);
+            return false;
+        }
+    }
+    return true;
+}
+
+// Issue the bulk copies of frames t0+lo .. t0+hi of this tile into the slot ring (producer lane).
 __device__ __forceinline__ void issue_group(TiledSmem &S, const float2 *__restrict__ ring, int R, size_t tile,
                                             long long t0, int lo, int hi, unsigned long long *bar)
 {
@@ -164,6 +207,22 @@ __device__ __forceinline__ void issue_group(TiledSmem &S, const float2 *__restri
         bulk_g2s(&S.buf[bp][0], ring + ((tile * (size_t)R + (size_t)rs) * kTile), (unsigned)(n * kTile * sizeof(float2)),
                  bar);
         a += n;
+    }
+}
+
+// Barrier among the consumer warps only (the producer warp does not take part).
+__device__ __forceinline__ void consumer_sync()
+{
+    asm volatile("bar.sync 1, %0;" ::"r"(kWarps * 32) : "memory");
+}
+
+// A consumer warp has finished reading the slot ring for one step.
+__device__ __forceinline__ void step_done(TiledSmem &S, int lane)
+{
+    __syncwarp();
+    if (lane == 0) {
+        __threadfence_block();
+        atomicAdd(&S.done, 1);
     }
 }
 
@@ -211,7 +270,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
 #pragma unroll
     for (int uu = 0; uu < 16; ++uu) {
         if (uu >= len) break;
-        pk_t a0 = 0ull, a1 = 0ull;
+        pk_t a[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
         for (int i = 0; i < kTw; ++i) {
             pk_t d = psub(xt[i], w[(i - uu) & (kTw - 1)]);
@@ -219,12 +278,9 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                 const bool v = (i - uu >= -base) && (i < hi_lim);
                 d = v ? d : 0ull;
             }
-            if (i & 1)
-                a1 = psq_acc(d, a1);
-            else
-                a0 = psq_acc(d, a0);
+            a[i & 3] = psq_acc(d, a[i & 3]);
         }
-        S.red[pend + uu][warp][lane] = phsum(a0) + phsum(a1);
+        S.red[pend + uu][warp][lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
         if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = ldf(-uu - 1);
     }
 }
@@ -251,7 +307,7 @@ __device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[k
 
 __device__ __forceinline__ void flush_partials(TiledSmem &S, float2 *__restrict__ acc, size_t M, size_t tile, int pend)
 {
-    __syncthreads();
+    consumer_sync();
     const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (j < pend) {
         float s = 0.f;
@@ -260,60 +316,89 @@ __device__ __forceinline__ void flush_partials(TiledSmem &S, float2 *__restrict_
         float2 *a = acc + (size_t)S.jd[j] * M + tile * kTile + lane;
         *a = kahan_add(*a, s);
     }
-    __syncthreads();
+    consumer_sync();
 }
 
-__global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
-                                                                    long long t0, int nb,
-                                                                    const __grid_constant__ DelaySchedule sched,
-                                                                    float2 *__restrict__ acc, int *__restrict__ err)
+__global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
+                                                                 long long t0, int nb,
+                                                                 const __grid_constant__ DelaySchedule sched,
+                                                                 float2 *__restrict__ acc, int *__restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
     const size_t tile = blockIdx.x;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
-    const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
+    const int nst = sched.nst;
 
     if (tid == 0) {
-        mbar_init(&S.bar[0], 1);
-        mbar_init(&S.bar[1], 1);
+        for (int b = 0; b < kFullBars; ++b) mbar_init(&S.full[b], 1);
+        S.done = 0;
+        S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();
-    // group 0: the block's own frames t0 .. t0 + K - 1
-    if (tid == 0) issue_group(S, ring, R, tile, t0, 0, kDelayBlock - 1, &S.bar[0]);
-    bool ok = mbar_wait_bounded(&S.bar[0], 0, kWaitLimitNs);
-    if (__syncthreads_or(!ok)) {
-        if (tid == 0) atomicExch(err, 1);
+    __syncthreads();  // the last barrier the producer warp takes part in
+
+    if (warp == kWarps) {
+        // producer: issue every copy group as soon as its rows are free and its barrier is reusable
+        if (lane == 0) {
+            int issued = 0;
+            for (int g = 0; g <= nst; ++g) {
+                const int need = (g == 0) ? 0 : sched.st[g - 1].need;
+                const int target = need * kWarps;
+                bool ok = true;
+                if (*(volatile int *)&S.done < target) {
+                    const unsigned long long tw = global_ns();
+                    while (*(volatile int *)&S.done < target) {
+                        if (*(volatile int *)&S.abort || *(volatile int *)err) {
+                            ok = false;
+                            break;
+                        }
+                        if (global_ns() - tw > kWaitLimitNs) {
+                            set_abort(S, err);
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                if (!ok) break;
+                __threadfence_block();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (g == 0)
+                    issue_group(S, ring, R, tile, t0, 0, kDelayBlock - 1, &S.full[0]);
+                else
+                    issue_group(S, ring, R, tile, t0, sched.st[g - 1].lo, sched.st[g - 1].hi, &S.full[g % kFullBars]);
+                issued = g + 1;
+            }
+            if (*(volatile int *)&S.abort || *(volatile int *)err) {
+                // let copies still in flight land (bounded) before the CTA's shared memory goes away
+                for (int g = issued - 1; g >= 0 && g >= issued - kFullBars; --g) {
+                    unsigned long long *bar = &S.full[g % kFullBars];
+                    const unsigned par = (unsigned)((g / kFullBars) & 1);
+                    const unsigned long long tw = global_ns();
+                    while (!mbar_try_wait(bar, par) && global_ns() - tw < kWaitLimitNs / 20) {
+                    }
+                }
+            }
+        }
         return;
     }
+
+    // consumers
+    const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
+    const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
+    wait_group(S, 0, err);
     pk_t xt[kTw];
 #pragma unroll
     for (int i = 0; i < kTw; ++i) xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane]);
-    __syncthreads();
+    step_done(S, lane);
 
+    // After a failed wait the loop still runs to the end (every shared-memory index stays in bounds,
+    // the numbers are wrong and the error word says so), so the consumer barriers never lose a warp.
     int pend = 0;
-    const int nst = sched.nst;
     for (int s = 0; s < nst; ++s) {
         const Stage st = sched.st[s];
-        const int g = s + 1;  // copy group of stage s
-        if (tid == 0) {
-            if (!st.prefetch) issue_group(S, ring, R, tile, t0, st.lo, st.hi, &S.bar[g & 1]);
-            if (s + 1 < nst) {
-                const Stage nx = sched.st[s + 1];
-                if (nx.prefetch) issue_group(S, ring, R, tile, t0, nx.lo, nx.hi, &S.bar[(g + 1) & 1]);
-            }
-        }
-        ok = mbar_wait_bounded(&S.bar[g & 1], (unsigned)((g >> 1) & 1), kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) {
-                atomicExch(err, 1);
-                // let copies still in flight land (bounded) before the CTA's shared memory goes away
-                mbar_wait_bounded(&S.bar[(g + 1) & 1], (unsigned)(((g + 1) >> 1) & 1), kWaitLimitNs / 20);
-            }
-            return;
-        }
+        wait_group(S, s + 1, err);
         for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
             const SubRun sr = sched.sr[r];
             if (pend + sr.len > 16) {
@@ -324,7 +409,7 @@ __global__ void __launch_bounds__(kWarps * 32, 1) k_delay_f32_tiled(const float2
             subrun_dispatch(S, xt, lane, warp, ta, sr.d0, sr.len, pend, hi_lim);
             pend += sr.len;
         }
-        __syncthreads();
+        step_done(S, lane);
     }
     if (pend) flush_partials(S, acc, M, tile, pend);
 }
@@ -396,7 +481,7 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
     cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(a.M / kTile);
-    k_delay_f32_tiled<<<grid, kWarps * 32, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, *a.sched, a.acc, a.err);
+    k_delay_f32_tiled<<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, *a.sched, a.acc, a.err);
     return cudaGetLastError();
 }
 

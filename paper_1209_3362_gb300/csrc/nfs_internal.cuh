@@ -117,8 +117,11 @@ struct SubRun {
 struct Stage {
     int sr0, nsr;    // sub-runs sr0 .. sr0+nsr-1
     int lo, hi;      // frames t0+lo .. t0+hi to load (lo > hi: nothing new)
-    int prefetch;    // 1: its loads may be issued while the previous stage computes
+    int need;        // the copy group of this stage may be issued once the consumers have finished
+                     // this many steps (step 0 = reading the block's own frames, step s+1 = stage s):
+                     // its slot-ring rows are then free and its mbarrier has been observed
 };
+constexpr int kFullBars = 4;       // copy-group mbarriers of the tiled kernel (group g uses g % 4)
 constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
 constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
 bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
