@@ -191,6 +191,7 @@ def main():
     ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
     ap.add_argument("--delays", type=int, default=0, help="use delays 1..n (profiling cases; not a bench value)")
     ap.add_argument("--block", type=int, default=0)
+    ap.add_argument("--delay-variant", type=int, default=0, help="fused delay kernel variant (0 = default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -243,6 +244,8 @@ def main():
     torch.cuda.synchronize()
 
     ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
+    if args.delay_variant:
+        ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
     pitch = ctx.get_option(P.OPT_PITCH)
     M = w.H * pitch

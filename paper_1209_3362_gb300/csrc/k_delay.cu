@@ -105,6 +105,20 @@ bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, s
     return true;
 }
 
+// Sub-runs are packed into batches of at most 16 delays in schedule order (a sub-run never splits).
+int count_delay_batches(const std::vector<SubRun> &srs)
+{
+    int n = 0, pend = 0;
+    for (const SubRun &sr : srs) {
+        if (pend + sr.len > 16) {
+            ++n;
+            pend = 0;
+        }
+        pend += sr.len;
+    }
+    return n + (pend ? 1 : 0);
+}
+
 // ------------------------------------------------------------------ PTX helpers
 
 __device__ __forceinline__ unsigned smem_u32(const void *p)
@@ -121,6 +135,11 @@ __device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity)
@@ -153,15 +172,20 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 constexpr int kWarps = 16;                       // consumer warps (16 frames each)
 constexpr int kTw = 16;                          // consecutive frames per consumer warp
-constexpr int kThreads = (kWarps + 1) * 32;      // + one producer warp that issues the copies
+constexpr int kProducer = kWarps;                // warp that issues the copy groups
+constexpr int kWriter = kWarps + 1;              // warp that reduces partial sums into the accumulators
+constexpr int kThreads = (kWarps + 2) * 32;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 static_assert(kWarps * kTw == kDelayBlock, "block = warps x frames per warp");
 
 struct TiledSmem {
     float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf
-    float red[16][kWarps][kTile];          // per-warp partial sums of up to 16 pending delays
-    int jd[16];                            // delay indices of the pending partials
+    float red[2][16][kWarps][kTile];       // per-warp partial sums of a batch of up to 16 delays, x2
+    int jd[2][16];                         // delay indices of a batch
+    int pend[2];                           // delays in a batch
     unsigned long long full[kFullBars];    // copy-group barriers (group g on full[g % kFullBars])
+    unsigned long long red_full[2];        // batch written by all consumer warps
+    unsigned long long red_free[2];        // batch drained by the writer
     int done;                              // consumer-warp step completions (kWarps per step)
     int abort;                             // set when a bounded wait gives up
 };
@@ -172,11 +196,10 @@ __device__ __forceinline__ void set_abort(TiledSmem &S, int *err)
     atomicExch(err, 1);
 }
 
-// Wait for copy group g (bounded; returns at once once any thread of the CTA has given up).
-__device__ __forceinline__ bool wait_group(TiledSmem &S, int g, int *err)
+// Wait for a phase of an mbarrier (bounded; returns at once once any thread of the launch has
+// given up).
+__device__ __forceinline__ bool wait_bar(TiledSmem &S, unsigned long long *bar, unsigned par, int *err)
 {
-    unsigned long long *bar = &S.full[g % kFullBars];
-    const unsigned par = (unsigned)((g / kFullBars) & 1);
     if (mbar_try_wait(bar, par)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, par)) {
@@ -188,6 +211,12 @@ __device__ __forceinline__ bool wait_group(TiledSmem &S, int g, int *err)
         }
     }
     return true;
+}
+
+// Wait for copy group g.
+__device__ __forceinline__ bool wait_group(TiledSmem &S, int g, int *err)
+{
+    return wait_bar(S, &S.full[g % kFullBars], (unsigned)((g / kFullBars) & 1), err);
 }
 
 // Issue the bulk copies of frames t0+lo .. t0+hi of this tile into the slot ring (producer lane).
@@ -208,12 +237,6 @@ __device__ __forceinline__ void issue_group(TiledSmem &S, const float2 *__restri
                  bar);
         a += n;
     }
-}
-
-// Barrier among the consumer warps only (the producer warp does not take part).
-__device__ __forceinline__ void consumer_sync()
-{
-    asm volatile("bar.sync 1, %0;" ::"r"(kWarps * 32) : "memory");
 }
 
 // A consumer warp has finished reading the slot ring for one step.
@@ -254,9 +277,16 @@ __device__ __forceinline__ float phsum(pk_t a)
 // older frame.  MASKED: drop pairs whose older frame is < 0 or whose new frame lies past the
 // block (i >= hi_lim).  WRAP: the 31 slot rows touched wrap around the slot ring, so every
 // address is taken modulo; otherwise they are immediate offsets from one base address.
-template <bool MASKED, bool WRAP>
+__device__ __forceinline__ float2 unpk(pk_t a)
+{
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(a));
+    return v;
+}
+
+template <bool MASKED, bool WRAP, bool PACKED>
 __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int base, int len,
-                                       int pend, int hi_lim)
+                                       float (*red)[kWarps][kTile], int pend, int hi_lim)
 {
     const float2 *col = &S.buf[0][lane];
     const float2 *p0 = col + (size_t)((base & (kSlotBuf - 1)) * kTile);
@@ -270,55 +300,67 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
 #pragma unroll
     for (int uu = 0; uu < 16; ++uu) {
         if (uu >= len) break;
-        pk_t a[4] = {0ull, 0ull, 0ull, 0ull};
+        if (PACKED) {
+            pk_t a[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-        for (int i = 0; i < kTw; ++i) {
-            pk_t d = psub(xt[i], w[(i - uu) & (kTw - 1)]);
-            if (MASKED) {
-                const bool v = (i - uu >= -base) && (i < hi_lim);
-                d = v ? d : 0ull;
+            for (int i = 0; i < kTw; ++i) {
+                pk_t d = psub(xt[i], w[(i - uu) & (kTw - 1)]);
+                if (MASKED) {
+                    const bool v = (i - uu >= -base) && (i < hi_lim);
+                    d = v ? d : 0ull;
+                }
+                a[i & 3] = psq_acc(d, a[i & 3]);
             }
-            a[i & 3] = psq_acc(d, a[i & 3]);
+            red[pend + uu][warp][lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
+        } else {
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < kTw; ++i) {
+                const float2 x = unpk(xt[i]), y = unpk(w[(i - uu) & (kTw - 1)]);
+                float dr = x.x - y.x, di = x.y - y.y;
+                if (MASKED) {
+                    const bool v = (i - uu >= -base) && (i < hi_lim);
+                    dr = v ? dr : 0.f;
+                    di = v ? di : 0.f;
+                }
+                a[i & 3] = fmaf(dr, dr, a[i & 3]);
+                a[i & 3] = fmaf(di, di, a[i & 3]);
+            }
+            red[pend + uu][warp][lane] = (a[0] + a[1]) + (a[2] + a[3]);
         }
-        S.red[pend + uu][warp][lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
         if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = ldf(-uu - 1);
     }
 }
 
 // Picks the sub-run variant for this warp (the choice is uniform within the warp).
+template <bool PACKED>
 __device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int ta,
-                                                int d0, int len, int pend, int hi_lim)
+                                                int d0, int len, float (*red)[kWarps][kTile], int pend, int hi_lim)
 {
     const int base = ta - d0;
     if (hi_lim <= 0 || base + kTw - 1 < 0) {  // no pair of this warp is valid
-        for (int u = 0; u < len; ++u) S.red[pend + u][warp][lane] = 0.f;
+        for (int u = 0; u < len; ++u) red[pend + u][warp][lane] = 0.f;
         return;
     }
     if (base - (len - 1) >= 0 && hi_lim >= kTw) {
         const int r0 = base & (kSlotBuf - 1);
         if (r0 >= 16 && r0 + 15 < kSlotBuf)
-            subrun<false, false>(S, xt, lane, warp, base, len, pend, hi_lim);
+            subrun<false, false, PACKED>(S, xt, lane, warp, base, len, red, pend, hi_lim);
         else
-            subrun<false, true>(S, xt, lane, warp, base, len, pend, hi_lim);
+            subrun<false, true, PACKED>(S, xt, lane, warp, base, len, red, pend, hi_lim);
     } else {
-        subrun<true, true>(S, xt, lane, warp, base, len, pend, hi_lim);
+        subrun<true, true, PACKED>(S, xt, lane, warp, base, len, red, pend, hi_lim);
     }
 }
 
-__device__ __forceinline__ void flush_partials(TiledSmem &S, float2 *__restrict__ acc, size_t M, size_t tile, int pend)
+// Consumer side of a batch hand-over: this warp's partial sums of batch b are written.
+__device__ __forceinline__ void hand_over(TiledSmem &S, int b, int lane)
 {
-    consumer_sync();
-    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (j < pend) {
-        float s = 0.f;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) s += S.red[j][w][lane];
-        float2 *a = acc + (size_t)S.jd[j] * M + tile * kTile + lane;
-        *a = kahan_add(*a, s);
-    }
-    consumer_sync();
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&S.red_full[b]);
 }
 
+template <bool PACKED>
 __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
                                                                  long long t0, int nb,
                                                                  const __grid_constant__ DelaySchedule sched,
@@ -332,14 +374,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
 
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_init(&S.full[b], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&S.red_full[b], kWarps);
+            mbar_init(&S.red_free[b], 1);
+        }
         S.done = 0;
         S.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();  // the last barrier the producer warp takes part in
+    __syncthreads();  // the only CTA-wide barrier
 
-    if (warp == kWarps) {
-        // producer: issue every copy group as soon as its rows are free and its barrier is reusable
+    if (warp == kProducer) {
+        // issue every copy group as soon as its rows are free and its barrier is reusable
         if (lane == 0) {
             int issued = 0;
             for (int g = 0; g <= nst; ++g) {
@@ -384,6 +430,32 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         return;
     }
 
+    if (warp == kWriter) {
+        // reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs
+        for (int k = 0; k < sched.nbatch; ++k) {
+            const int b = k & 1;
+            wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err);
+            const int pend = S.pend[b];
+            float2 *base = acc + tile * kTile + lane;
+            float2 old[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (j < pend) old[j] = base[(size_t)S.jd[b][j] * M];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (j < pend) {
+                    float s = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kWarps; ++w) s += S.red[b][j][w][lane];
+                    base[(size_t)S.jd[b][j] * M] = kahan_add(old[j], s);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S.red_free[b]);
+        }
+        return;
+    }
+
     // consumers
     const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
     const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
@@ -394,24 +466,34 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
     step_done(S, lane);
 
     // After a failed wait the loop still runs to the end (every shared-memory index stays in bounds,
-    // the numbers are wrong and the error word says so), so the consumer barriers never lose a warp.
-    int pend = 0;
+    // the numbers are wrong and the error word says so), so no barrier ever loses a warp.
+    int pend = 0, batch = 0;
+    auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 2
+        if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err);
+    };
+    open_batch(0);
     for (int s = 0; s < nst; ++s) {
         const Stage st = sched.st[s];
         wait_group(S, s + 1, err);
         for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
             const SubRun sr = sched.sr[r];
             if (pend + sr.len > 16) {
-                flush_partials(S, acc, M, tile, pend);
+                if (tid == 0) S.pend[batch & 1] = pend;
+                hand_over(S, batch & 1, lane);
+                ++batch;
                 pend = 0;
+                open_batch(batch);
             }
-            if (tid < sr.len) S.jd[pend + tid] = sr.j0 + tid;
-            subrun_dispatch(S, xt, lane, warp, ta, sr.d0, sr.len, pend, hi_lim);
+            if (tid < sr.len) S.jd[batch & 1][pend + tid] = sr.j0 + tid;
+            subrun_dispatch<PACKED>(S, xt, lane, warp, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim);
             pend += sr.len;
         }
         step_done(S, lane);
     }
-    if (pend) flush_partials(S, acc, M, tile, pend);
+    if (pend) {
+        if (tid == 0) S.pend[batch & 1] = pend;
+        hand_over(S, batch & 1, lane);
+    }
 }
 
 // ------------------------------------------------------------------ simple block kernel (variant 1)
@@ -476,12 +558,38 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
         return cudaSuccess;
     }
     if (a.nb > kDelayBlock || (a.M % kTile) != 0) return cudaErrorInvalidValue;
-    if (a.sched->nst == 0) return cudaSuccess;  // only tau = 0 in the list
+    // Stages whose smallest delay exceeds the block's last frame have no valid pair yet (early
+    // blocks of a sequence): leave them out of this launch, with the batches they would fill.
+    DelaySchedule sc = *a.sched;
+    const long long tlast = a.t0 + a.nb - 1;
+    int nst = 0;
+    while (nst < sc.nst && (long long)sc.sr[sc.st[nst].sr0].d0 <= tlast) ++nst;
+    if (nst == 0) return cudaSuccess;  // nothing to add (or only tau = 0 in the list)
+    {
+        int nb_batches = 0, pend = 0;
+        for (int r = 0; r < sc.st[nst - 1].sr0 + sc.st[nst - 1].nsr; ++r) {
+            if (pend + sc.sr[r].len > 16) {
+                ++nb_batches;
+                pend = 0;
+            }
+            pend += sc.sr[r].len;
+        }
+        sc.nbatch = nb_batches + (pend ? 1 : 0);
+        sc.nst = nst;
+    }
     const size_t smem = sizeof(TiledSmem);
-    cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const unsigned grid = (unsigned)(a.M / kTile);
-    k_delay_f32_tiled<<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, *a.sched, a.acc, a.err);
+    if (variant == 2) {
+        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_delay_f32_tiled<false><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.err);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        k_delay_f32_tiled<true><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.err);
+    }
     return cudaGetLastError();
 }
 

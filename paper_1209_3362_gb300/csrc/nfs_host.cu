@@ -487,6 +487,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
             if (!c->sched) return bail(NFS_ENOMEM);
             c->sched->nsr = (int)srs.size();
             c->sched->nst = (int)sts.size();
+            c->sched->nbatch = count_delay_batches(srs);
             std::copy(srs.begin(), srs.end(), c->sched->sr);
             std::copy(sts.begin(), sts.end(), c->sched->st);
         }
@@ -697,7 +698,7 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             c->fft_chunk = (int)v;
             return NFS_OK;
         case NFS_OPT_DELAY_VARIANT:
-            if (v < 0 || v > 1) return NFS_EINVAL;
+            if (v < 0 || v > 2) return NFS_EINVAL;
             c->delay_variant = (int)v;
             return NFS_OK;
         case NFS_OPT_FFT_GENERIC:

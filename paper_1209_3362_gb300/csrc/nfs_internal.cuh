@@ -125,12 +125,14 @@ constexpr int kFullBars = 4;       // copy-group mbarriers of the tiled kernel (
 constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
 constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
 bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
+int count_delay_batches(const std::vector<SubRun> &subruns);  // batches the consumers hand to the writer
 
 // The schedule travels by value in the kernel parameters (constant bank): uniform, cached reads.
 constexpr int kMaxSubRuns = 256;
 constexpr int kMaxSchedStages = 128;
 struct DelaySchedule {
     int nsr, nst;
+    int nbatch;  // batches of up to 16 delays whose partial sums are reduced together
     SubRun sr[kMaxSubRuns];
     Stage st[kMaxSchedStages];
 };

@@ -209,8 +209,11 @@ def test_delay_kernel_variants_agree(long64):
     fr, delays, ref = long64
     a = _with_variant(fr, delays, 32, 0)
     b = _with_variant(fr, delays, 32, 1)
-    assert rel_err(a, ref) <= TOL_F32 and rel_err(b, ref) <= TOL_F32
+    c = _with_variant(fr, delays, 32, 2)
+    for x in (a, b, c):
+        assert rel_err(x, ref) <= TOL_F32
     np.testing.assert_allclose(a["D"], b["D"], rtol=2e-6, atol=0)
+    np.testing.assert_allclose(a["D"], c["D"], rtol=2e-6, atol=0)
 
 
 def test_sparse_delays_with_large_gaps(oracle_lib):
