@@ -186,27 +186,57 @@ struct TiledSmem {
     unsigned long long full[kFullBars];    // copy-group barriers (group g on full[g % kFullBars])
     unsigned long long red_full[2];        // batch written by all consumer warps
     unsigned long long red_free[2];        // batch drained by the writer
-    int done;                              // consumer-warp step completions (kWarps per step)
+    int done;                              // consumer-warp step completions, all warps (diagnostics)
     int abort;                             // set when a bounded wait gives up
+    int wsteps[kWarps];                    // per consumer warp: steps completed (the producer waits for
+                                           // the minimum: a sum would let fast warps count for a slow one)
+    int wbatches[kWarps];                  // per consumer warp: batches handed over (diagnostics)
+    int wdrained;                          // batches the writer has drained (diagnostics)
 };
 
-__device__ __forceinline__ void set_abort(TiledSmem &S, int *err)
+// err[0] = 1 once any wait of the launch gives up; the first thread to give up records in err[1..]
+// which wait it was: kind (1 copy group, 2 batch written, 3 batch drained, 4 producer progress),
+// CTA, warp, group or batch index, polls, globaltimer ns and clock64 cycles spent (low 31 bits
+// of each, saturated), and the CTA's progress counter.
+__device__ __forceinline__ void set_abort(TiledSmem &S, int *err, int kind, int index, long long polls,
+                                          unsigned long long ns, long long cycles)
 {
     *(volatile int *)&S.abort = 1;
+    if (atomicCAS(err + 1, 0, kind) == 0) {
+        err[2] = (int)blockIdx.x;
+        err[3] = (int)(threadIdx.x >> 5);
+        err[4] = index;
+        err[5] = (int)(polls > 0x7fffffffLL ? 0x7fffffffLL : polls);
+        err[6] = (int)(ns > 0x7fffffffull ? 0x7fffffffull : ns);
+        err[7] = (int)(cycles > 0x7fffffffLL ? 0x7fffffffLL : cycles);
+        err[8] = *(volatile int *)&S.done;
+        err[9] = *(volatile int *)&S.wdrained;
+        for (int w = 0; w < kWarps; ++w) {
+            err[10 + w] = ((volatile int *)S.wsteps)[w];
+            err[10 + kWarps + w] = ((volatile int *)S.wbatches)[w];
+        }
+    }
+    __threadfence();
     atomicExch(err, 1);
 }
+constexpr long long kMinPolls = 100000;  // a wait gives up only after this many polls AND the time limit
 
 // Wait for a phase of an mbarrier (bounded; returns at once once any thread of the launch has
 // given up).
-__device__ __forceinline__ bool wait_bar(TiledSmem &S, unsigned long long *bar, unsigned par, int *err)
+__device__ __forceinline__ bool wait_bar(TiledSmem &S, unsigned long long *bar, unsigned par, int *err, int kind,
+                                         int index)
 {
     if (mbar_try_wait(bar, par)) return true;
     const unsigned long long t0 = global_ns();
+    const long long c0 = clock64();
+    long long polls = 0;
     while (!mbar_try_wait(bar, par)) {
         // give up at once when this CTA or any other CTA of the launch has given up
         if (*(volatile int *)&S.abort || *(volatile int *)err) return false;
-        if (global_ns() - t0 > kWaitLimitNs) {
-            set_abort(S, err);
+        ++polls;
+        const unsigned long long dt = global_ns() - t0;
+        if (polls > kMinPolls && dt > kWaitLimitNs) {
+            set_abort(S, err, kind, index, polls, dt, clock64() - c0);
             return false;
         }
     }
@@ -216,7 +246,7 @@ __device__ __forceinline__ bool wait_bar(TiledSmem &S, unsigned long long *bar, 
 // Wait for copy group g.
 __device__ __forceinline__ bool wait_group(TiledSmem &S, int g, int *err)
 {
-    return wait_bar(S, &S.full[g % kFullBars], (unsigned)((g / kFullBars) & 1), err);
+    return wait_bar(S, &S.full[g % kFullBars], (unsigned)((g / kFullBars) & 1), err, 1, g);
 }
 
 // Issue the bulk copies of frames t0+lo .. t0+hi of this tile into the slot ring (producer lane).
@@ -245,8 +275,18 @@ __device__ __forceinline__ void step_done(TiledSmem &S, int lane)
     __syncwarp();
     if (lane == 0) {
         __threadfence_block();
+        ++((volatile int *)S.wsteps)[threadIdx.x >> 5];
         atomicAdd(&S.done, 1);
     }
+}
+
+// Steps completed by every consumer warp.
+__device__ __forceinline__ int min_steps(TiledSmem &S)
+{
+    int m = 0x7fffffff;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) m = min(m, ((volatile int *)S.wsteps)[w]);
+    return m;
 }
 
 // Packed FP32 pairs (Blackwell f32x2 arithmetic): a complex value is one 64-bit register
@@ -357,7 +397,10 @@ __device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[k
 __device__ __forceinline__ void hand_over(TiledSmem &S, int b, int lane)
 {
     __syncwarp();
-    if (lane == 0) mbar_arrive(&S.red_full[b]);
+    if (lane == 0) {
+        mbar_arrive(&S.red_full[b]);
+        ++((volatile int *)S.wbatches)[threadIdx.x >> 5];
+    }
 }
 
 template <bool PACKED>
@@ -380,6 +423,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         }
         S.done = 0;
         S.abort = 0;
+        S.wdrained = 0;
+        for (int w = 0; w < kWarps; ++w) S.wsteps[w] = S.wbatches[w] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();  // the only CTA-wide barrier
@@ -390,17 +435,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
             int issued = 0;
             for (int g = 0; g <= nst; ++g) {
                 const int need = (g == 0) ? 0 : sched.st[g - 1].need;
-                const int target = need * kWarps;
                 bool ok = true;
-                if (*(volatile int *)&S.done < target) {
+                if (min_steps(S) < need) {
                     const unsigned long long tw = global_ns();
-                    while (*(volatile int *)&S.done < target) {
+                    const long long c0 = clock64();
+                    long long polls = 0;
+                    while (min_steps(S) < need) {
                         if (*(volatile int *)&S.abort || *(volatile int *)err) {
                             ok = false;
                             break;
                         }
-                        if (global_ns() - tw > kWaitLimitNs) {
-                            set_abort(S, err);
+                        ++polls;
+                        const unsigned long long dt = global_ns() - tw;
+                        if (polls > kMinPolls && dt > kWaitLimitNs) {
+                            set_abort(S, err, 4, g, polls, dt, clock64() - c0);
                             ok = false;
                             break;
                         }
@@ -434,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         // reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs
         for (int k = 0; k < sched.nbatch; ++k) {
             const int b = k & 1;
-            wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err);
+            wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err, 2, k);
             const int pend = S.pend[b];
             float2 *base = acc + tile * kTile + lane;
             float2 old[16];
@@ -451,7 +499,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                 }
             }
             __syncwarp();
-            if (lane == 0) mbar_arrive(&S.red_free[b]);
+            if (lane == 0) {
+                mbar_arrive(&S.red_free[b]);
+                *(volatile int *)&S.wdrained = k + 1;
+            }
         }
         return;
     }
@@ -469,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
     // the numbers are wrong and the error word says so), so no barrier ever loses a warp.
     int pend = 0, batch = 0;
     auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 2
-        if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err);
+        if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err, 3, k);
     };
     open_batch(0);
     for (int s = 0; s < nst; ++s) {

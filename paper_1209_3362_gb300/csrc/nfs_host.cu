@@ -475,8 +475,8 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
             return bail(NFS_ECUDA);
     }
     if (build_bins(c)) return bail(NFS_ECUDA);
-    if ((rc = alloc_dev(c, (void **)&c->d_err, sizeof(int)))) return bail(rc);
-    if (cudaMemset(c->d_err, 0, sizeof(int)) != cudaSuccess) return bail(NFS_ECUDA);
+    if ((rc = alloc_dev(c, (void **)&c->d_err, sizeof(int) * kDelayErrWords))) return bail(rc);
+    if (cudaMemset(c->d_err, 0, sizeof(int) * kDelayErrWords) != cudaSuccess) return bail(NFS_ECUDA);
     if (c->f32()) {
         std::vector<SubRun> srs;
         std::vector<Stage> sts;
@@ -602,11 +602,20 @@ int nfs_structure_function(nfs_ctx *c, double *D, int64_t *bin_counts, int64_t *
     }, "bin");
     if (rc) return rc;
     CK(c, cudaMemcpyAsync(D, c->d_D, sizeof(double) * (size_t)c->nd * c->nq, cudaMemcpyDeviceToHost, c->stream));
-    int dev_err = 0;
-    CK(c, cudaMemcpyAsync(&dev_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    int dev_err[kDelayErrWords] = {};
+    CK(c, cudaMemcpyAsync(dev_err, c->d_err, sizeof(dev_err), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    if (dev_err) {
-        c->errmsg = "delay kernel: a bounded wait for its shared-memory copies gave up";
+    if (dev_err[0]) {
+        char buf[1024];
+        int n = snprintf(buf, sizeof(buf),
+                         "delay kernel: a bounded wait gave up (kind %d, cta %d, warp %d, index %d, polls %d, ns %d, "
+                         "cycles %d, progress %d, drained %d; steps/batches per warp:",
+                         dev_err[1], dev_err[2], dev_err[3], dev_err[4], dev_err[5], dev_err[6], dev_err[7],
+                         dev_err[8], dev_err[9]);
+        for (int w = 0; w < 16 && n > 0 && n < (int)sizeof(buf) - 16; ++w)
+            n += snprintf(buf + n, sizeof(buf) - n, " %d/%d", dev_err[10 + w], dev_err[26 + w]);
+        if (n > 0 && n < (int)sizeof(buf) - 2) snprintf(buf + n, sizeof(buf) - n, ")");
+        c->errmsg = buf;
         if (c->err == NFS_OK) c->err = NFS_ETIMEOUT;
         return c->err;
     }

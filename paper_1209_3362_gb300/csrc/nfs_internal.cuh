@@ -122,6 +122,7 @@ struct Stage {
                      // its slot-ring rows are then free and its mbarrier has been observed
 };
 constexpr int kFullBars = 4;       // copy-group mbarriers of the tiled kernel (group g uses g % 4)
+constexpr int kDelayErrWords = 48; // status words of the tiled kernel
 constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
 constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
 bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
@@ -148,7 +149,7 @@ struct DelayArgs {
     int nd;
     float2 *acc;  // [nd][M] (Kahan sum, compensation)
     const DelaySchedule *sched;  // host copy; NULL = no tiled schedule (one-thread-per-mode kernel)
-    int *err;     // device status word: set when a bounded wait in the kernel gives up
+    int *err;     // device status words (kDelayErrWords): [0] set when a bounded wait gives up, [1..] where
     int tau_max;
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
