@@ -40,11 +40,31 @@ METRIC = "frames/s at 2048²,200 delays (fused FP32 vs plain FP64, err≤2e-5); 
 
 
 def load_peaks():
+    """(HBM GB/s, SM max MHz, source) from MEASURED_PEAKS.json, else the recipe's fallback."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return float(d["hbm_gbs"]), "measured"
-    return 6800.0, "fallback"
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    return 6800.0, 2070.0, "fallback"
+
+
+FP32_LANES_PER_SM = 128      # FP32 lanes of a Blackwell SM
+FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squares, 2 additions
+
+# DRAM traffic of the fused delay kernel per algorithmic byte, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
+# applies only to the kernel source it was measured on: any change to these files voids it.
+DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
+NCU_DELAY_CALIBRATION = {"sha256": "b8e45502998e78467180a7b75171690518f0df1da4f5e00bbb9c862b1b55308c",
+                         "dram_bytes_per_alg_byte": 0.9953}
+
+
+def delay_kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in DELAY_KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()
 
 
 class ClockSampler:
@@ -230,7 +250,9 @@ def main():
 
     P.build()
     P.load_library()
-    hbm_peak, peak_src = load_peaks()
+    hbm_peak, sm_mhz, peak_src = load_peaks()
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
 
     # ---- inputs: the rank's own sequence, generated on its GPU, resident in HBM
     src = S.OUFrameSource(w.H, w.W, w.Dc, w.gamma0, eps=w.eps, seed=w.seed + 7919 * rank, device="cuda",
@@ -247,8 +269,7 @@ def main():
     if args.delay_variant:
         ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
-    pitch = ctx.get_option(P.OPT_PITCH)
-    M = w.H * pitch
+    M = (w.H * (w.W // 2 + 1) + 31) // 32 * 32  # modes per spectrum (column-major, padded to 32)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def step():
@@ -282,15 +303,29 @@ def main():
     tim = ctx.timings()
     D32 = res["D"]
 
-    # ---- roofline of the fused delay kernel
+    # ---- roofline of the fused delay kernel (the dominant kernel)
+    # Its arithmetic intensity (6 flops per pair and mode against each ring value and accumulator
+    # moved once per block) lies above the FP32 ridge point, so the roofline that bounds it is the
+    # FP32 ALU peak; the HBM fraction the metric asks for is reported beside it.
     alg_bytes, n_launch, pairs = delay_block_bytes(w.delays, w.N, K, M)
+    modes = w.H * (w.W // 2 + 1)
+    alg_flops = FLOPS_PER_PAIR_MODE * pairs * modes
     delay_ms, delay_n = tim["delay"]
     per_launch_ms = delay_ms / max(delay_n, 1)
-    achieved = (alg_bytes / n_launch) / (per_launch_ms / 1000.0) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None, "kernel": "k_delay_f32_tiled",
-                "peak_source": f"{peak_src} hbm_gbs", "bytes_per_launch": alg_bytes / n_launch,
-                "launch_ms": per_launch_ms}
+    per_launch_s = per_launch_ms / 1000.0
+    achieved = (alg_flops / n_launch) / per_launch_s / 1e12
+    hbm_achieved = (alg_bytes / n_launch) / per_launch_s / 1e9
+    cal = NCU_DELAY_CALIBRATION
+    traffic = None
+    if cal["sha256"] and cal["sha256"] == delay_kernel_sha():
+        traffic = cal["dram_bytes_per_alg_byte"] * alg_bytes / n_launch
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak, "traffic": traffic, "kernel": "k_delay_f32_tiled",
+                "peak_source": f"derived: {n_sm} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_mhz:.0f} MHz",
+                "flops_per_launch": alg_flops / n_launch, "bytes_per_launch": alg_bytes / n_launch,
+                "launch_ms": per_launch_ms, "launches": n_launch,
+                "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
+                        "peak_source": f"{peak_src} hbm_gbs"}}
     stage_ms = {k: v[0] / args.steps for k, v in tim.items()}
 
     # ---- end to end from pinned host memory
@@ -361,7 +396,7 @@ def main():
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
                            "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "
-                           f"{ctx_bytes(w, K, pitch) / 1e9:.1f} GB per rank)"},
+                           f"{ctx_bytes(w, K, M) / 1e9:.1f} GB per rank)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "plain_f64_gpu": plain, "stage_ms_per_step": stage_ms,
                 "delay_pairs_per_step": pairs}
@@ -370,8 +405,8 @@ def main():
         dist.destroy_process_group()
 
 
-def ctx_bytes(w, K, pitch):
-    return (w.delays[-1] + K) * w.H * pitch * 8
+def ctx_bytes(w, K, M):
+    return (w.delays[-1] + K) * M * 8
 
 
 if __name__ == "__main__":
