@@ -67,10 +67,15 @@ struct nfs_ctx {
     std::vector<int32_t> delays;
     int tau_max = 0;
 
-    uint16_t *d_stage[2] = {nullptr, nullptr};
+    // Host-push staging: a device ring of n_slots copy chunks of copy_frames frames each, so the
+    // copy stream can run up to about two delay blocks ahead of the kernels; pageable sources pass
+    // through two pinned host chunks first.
+    int copy_frames = 1, n_slots = 2;
+    uint16_t *d_stage = nullptr;
     uint16_t *h_stage[2] = {nullptr, nullptr};
-    cudaEvent_t ev_filled[2] = {nullptr, nullptr}, ev_free[2] = {nullptr, nullptr}, ev_copied[2] = {nullptr, nullptr};
-    int stage_i = 0;
+    std::vector<cudaEvent_t> ev_filled, ev_free;
+    cudaEvent_t ev_hcopied[2] = {nullptr, nullptr};
+    long long stage_i = 0, hstage_i = 0;
 
     unsigned long long *d_sums = nullptr;
     float *d_ref = nullptr;
@@ -269,12 +274,12 @@ void free_all(nfs_ctx *c)
         cudaEventDestroy(p.b);
     }
     for (auto e : c->pool) cudaEventDestroy(e);
+    cudaFree(c->d_stage);
+    for (auto e : c->ev_filled) cudaEventDestroy(e);
+    for (auto e : c->ev_free) cudaEventDestroy(e);
     for (int i = 0; i < 2; ++i) {
-        cudaFree(c->d_stage[i]);
         if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
-        if (c->ev_filled[i]) cudaEventDestroy(c->ev_filled[i]);
-        if (c->ev_free[i]) cudaEventDestroy(c->ev_free[i]);
-        if (c->ev_copied[i]) cudaEventDestroy(c->ev_copied[i]);
+        if (c->ev_hcopied[i]) cudaEventDestroy(c->ev_hcopied[i]);
     }
     cudaFree(c->d_sums);
     cudaFree(c->d_ref);
@@ -443,13 +448,23 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
         return bail(NFS_ECUDA);
-    for (int i = 0; i < 2; ++i) {
-        if (cudaEventCreateWithFlags(&c->ev_filled[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_copied[i], cudaEventDisableTiming) != cudaSuccess)
-            return bail(NFS_ECUDA);
-        if ((rc = alloc_dev(c, (void **)&c->d_stage[i], c->frame_bytes() * (size_t)c->stage_frames))) return bail(rc);
+    // copy chunks of up to 256 MB; the device staging ring covers two delay blocks, at most 4 GB
+    c->copy_frames = (int)std::max<size_t>(1, std::min<size_t>(64, (256u << 20) / c->frame_bytes()));
+    {
+        const size_t cap = std::max<size_t>(2, (size_t(4) << 30) / (c->frame_bytes() * (size_t)c->copy_frames));
+        const size_t want = std::max<size_t>(2, (2 * (size_t)c->K + c->copy_frames - 1) / c->copy_frames);
+        c->n_slots = (int)std::min(cap, want);
     }
+    c->ev_filled.assign((size_t)c->n_slots, nullptr);
+    c->ev_free.assign((size_t)c->n_slots, nullptr);
+    for (int i = 0; i < c->n_slots; ++i)
+        if (cudaEventCreateWithFlags(&c->ev_filled[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_free[i], cudaEventDisableTiming) != cudaSuccess)
+            return bail(NFS_ECUDA);
+    for (int i = 0; i < 2; ++i)
+        if (cudaEventCreateWithFlags(&c->ev_hcopied[i], cudaEventDisableTiming) != cudaSuccess) return bail(NFS_ECUDA);
+    if ((rc = alloc_dev(c, (void **)&c->d_stage, c->frame_bytes() * (size_t)c->copy_frames * c->n_slots)))
+        return bail(rc);
     const size_t ring_bytes = (size_t)c->R * c->g.M * c->csize();
     const size_t acc_bytes = (size_t)c->nd * c->g.M * c->asize();
     if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * kMaxChunk))) return bail(rc);
@@ -531,42 +546,49 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
     const bool locked = is_page_locked(h);
     if (!locked && !c->h_stage[0]) {
         for (int i = 0; i < 2; ++i) {
-            cudaError_t e = cudaMallocHost((void **)&c->h_stage[i], c->frame_bytes() * (size_t)c->stage_frames);
+            cudaError_t e = cudaMallocHost((void **)&c->h_stage[i], c->frame_bytes() * (size_t)c->copy_frames);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return NFS_ENOMEM;
             }
         }
     }
-    const int cap = std::min(c->fft_chunk, c->stage_frames);
     long long done = 0;
     int last = -1;
     while (done < n) {
-        const int nf = next_chunk(c, n - done, cap);
-        const int i = c->stage_i;
-        c->stage_i ^= 1;
-        const size_t bytes = c->frame_bytes() * (size_t)nf;
+        const int nc = (int)std::min<long long>(c->copy_frames, n - done);
+        const int slot = (int)(c->stage_i++ % c->n_slots);
+        const size_t bytes = c->frame_bytes() * (size_t)nc;
+        uint16_t *dst = c->d_stage + (size_t)slot * c->copy_frames * c->g.HW;
         const uint16_t *src = h + (size_t)done * c->g.HW;
-        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[i], 0));
+        // the kernels that read this slot last time must be done before it is overwritten
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[slot], 0));
+        int hs = -1;
         if (!locked) {
-            CK(c, cudaEventSynchronize(c->ev_copied[i]));
-            memcpy(c->h_stage[i], src, bytes);
-            src = c->h_stage[i];
+            hs = (int)(c->hstage_i++ & 1);
+            CK(c, cudaEventSynchronize(c->ev_hcopied[hs]));
+            memcpy(c->h_stage[hs], src, bytes);
+            src = c->h_stage[hs];
         }
         rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
-            return cudaMemcpyAsync(c->d_stage[i], src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
         }, "h2d");
         if (rc) return rc;
-        CK(c, cudaEventRecord(c->ev_copied[i], c->copy_stream));
-        CK(c, cudaEventRecord(c->ev_filled[i], c->copy_stream));
-        CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[i], 0));
-        rc = process_chunk(c, c->d_stage[i], nf);
-        if (rc) return rc;
-        CK(c, cudaEventRecord(c->ev_free[i], c->stream));
-        done += nf;
-        last = i;
+        if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
+        CK(c, cudaEventRecord(c->ev_filled[slot], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[slot], 0));
+        for (int o = 0; o < nc;) {
+            const int nf = next_chunk(c, nc - o, c->fft_chunk);
+            rc = process_chunk(c, dst + (size_t)o * c->g.HW, nf);
+            if (rc) return rc;
+            o += nf;
+        }
+        CK(c, cudaEventRecord(c->ev_free[slot], c->stream));
+        done += nc;
+        last = slot;
     }
-    if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_copied[last]));
+    // copies run in order on the copy stream: when the last one is done the caller's buffer is free
+    if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_filled[last]));
     return c->err;
 }
 
