@@ -144,6 +144,10 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 #define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel: 0 = tiled, packed f32x2 math (default);
                                    1 = one thread per mode; 2 = tiled, scalar FP32 math */
 #define NFS_OPT_FFT_GENERIC 8   /* 1 = generic FFT kernels even where size-specialised ones exist */
+#define NFS_OPT_TEST_STALL_GROUP 9 /* test hook (default -1 = off): the tiled delay kernel's producer
+                                      stops issuing copies from this group on, so a consumer's bounded
+                                      wait runs out (~2 s) and the call returns NFS_ETIMEOUT; checks
+                                      the failure path without faulting the GPU */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);
 int nfs_get_option(const nfs_ctx *ctx, int key, int64_t *value);
 
@@ -168,6 +172,36 @@ int nfs_reset_timings(nfs_ctx *ctx);
  * Number of kernel launches the context has issued since creation (all stages, both paths).
  */
 int64_t nfs_launch_count(const nfs_ctx *ctx);
+
+/*
+ * ---------------------------------------------------------------- Eq. 1 fit
+ * Per radial bin b, fit D_b(tau) = 2 A_b [1 - exp(-Gamma_b tau)] + 2 B_b to the structure function,
+ * i.e. Eq. 1 with the intermediate scattering function f = exp(-Gamma tau), A = a T I_s (static
+ * amplitude), B = a B (noise background).  Loss per bin: sum over delays of the squared residual.
+ */
+#define NFS_FIT_GAUSS_NEWTON 0 /* Levenberg-Marquardt-damped Gauss-Newton, A, B >= 0, Gamma > 0 */
+#define NFS_FIT_ADAM 1         /* Adam on theta = theta_0 (1 + u), step 1e-2 in u */
+
+/*
+ * Fit every bin of the context's structure function (D = NULL: the current result, as
+ * nfs_structure_function gives it; else a caller-owned HOST array [n_delays][n_qbins]).  Delays
+ * with no pair and tau = 0 are left out.  A, B, Gamma: HOST arrays [n_qbins], initial values in,
+ * fitted values out.  iters: Gauss-Newton or Adam steps.  Synchronises; NFS_ESTATE if no delay
+ * has data.
+ */
+int nfs_fit(nfs_ctx *ctx, const double *D, float *A, float *B, float *Gamma, int iters, int method);
+
+/*
+ * Device-level pieces for autograd drivers.  All pointers DEVICE memory, D [n_delays][n_bins]
+ * (bins fastest), tau [n_delays], parameters and outputs [n_bins]; stream = cudaStream_t or NULL.
+ * nfs_fit_loss_grad: loss[b] = sum_j r_j^2 and its gradients (gA, gB, gGamma may be NULL).
+ * nfs_fit_gauss_newton: iters damped Gauss-Newton steps in place (lambda: initial damping).
+ * Asynchronous on the stream; NFS_EINVAL for bad arguments, NFS_ECUDA if the launch fails.
+ */
+int nfs_fit_loss_grad(const float *D, const float *tau, int n_delays, int n_bins, const float *A, const float *B,
+                      const float *Gamma, float *loss, float *gA, float *gB, float *gGamma, void *stream);
+int nfs_fit_gauss_newton(const float *D, const float *tau, int n_delays, int n_bins, float *A, float *B,
+                         float *Gamma, int iters, float lambda, void *stream);
 
 /*
  * ---------------------------------------------------------------- analysis without allocation

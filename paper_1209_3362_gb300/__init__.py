@@ -37,6 +37,9 @@ OPT_PATH = 5
 OPT_FFT_CHUNK = 6
 OPT_DELAY_VARIANT = 7
 OPT_FFT_GENERIC = 8
+OPT_TEST_STALL_GROUP = 9
+FIT_GAUSS_NEWTON = 0
+FIT_ADAM = 1
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
 
 _lib = None
@@ -84,6 +87,9 @@ def load_library(path: Optional[str] = None):
         "nfs_reset_timings": (I, [V]),
         "nfs_launch_count": (I64, [V]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
+        "nfs_fit": (I, [V, V, V, V, V, I, I]),
+        "nfs_fit_loss_grad": (I, [V, V, I, I, V, V, V, V, V, V, V, V]),
+        "nfs_fit_gauss_newton": (I, [V, V, I, I, V, V, V, I, ctypes.c_float, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -233,6 +239,16 @@ class NFS:
 
     def reset_timings(self):
         self._check(self._L.nfs_reset_timings(self._h), "nfs_reset_timings")
+
+    def fit(self, A, B, Gamma, iters: int = 50, method: int = FIT_GAUSS_NEWTON, D=None):
+        """Fit Eq. 1 per bin (nfs_fit); initial A, B, Gamma in, fitted arrays returned."""
+        nq = self.n_qbins
+        a = np.ascontiguousarray(np.asarray(A, np.float32).reshape(nq)).copy()
+        b = np.ascontiguousarray(np.asarray(B, np.float32).reshape(nq)).copy()
+        g = np.ascontiguousarray(np.asarray(Gamma, np.float32).reshape(nq)).copy()
+        d = None if D is None else np.ascontiguousarray(np.asarray(D, np.float64))
+        self._check(self._L.nfs_fit(self._h, _ptr(d), _ptr(a), _ptr(b), _ptr(g), int(iters), int(method)), "nfs_fit")
+        return a, b, g
 
 
 def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) -> dict:

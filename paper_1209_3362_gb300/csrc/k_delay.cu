@@ -407,7 +407,8 @@ template <bool PACKED>
 __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
                                                                  long long t0, int nb,
                                                                  const __grid_constant__ DelaySchedule sched,
-                                                                 float2 *__restrict__ acc, int *__restrict__ err)
+                                                                 float2 *__restrict__ acc, int nd,
+                                                                 int *__restrict__ err, int stall_group)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
@@ -425,6 +426,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         S.abort = 0;
         S.wdrained = 0;
         for (int w = 0; w < kWarps; ++w) S.wsteps[w] = S.wbatches[w] = 0;
+        for (int b = 0; b < 2; ++b) {
+            S.pend[b] = 0;
+            for (int j = 0; j < 16; ++j) S.jd[b][j] = 0;
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();  // the only CTA-wide barrier
@@ -434,6 +439,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         if (lane == 0) {
             int issued = 0;
             for (int g = 0; g <= nst; ++g) {
+                // test hook: issue nothing from group stall_group on (every group issued before it
+                // is consumed before the consumers reach it, so no copy is left in flight)
+                if (g == stall_group) break;
                 const int need = (g == 0) ? 0 : sched.st[g - 1].need;
                 bool ok = true;
                 if (min_steps(S) < need) {
@@ -482,20 +490,25 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         // reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs
         for (int k = 0; k < sched.nbatch; ++k) {
             const int b = k & 1;
-            wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err, 2, k);
+            // After a failed wait the batch may not be written yet: stop touching global memory
+            // (the launch's results are void and the error word says so).
+            if (!wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err, 2, k)) break;
             const int pend = S.pend[b];
             float2 *base = acc + tile * kTile + lane;
             float2 old[16];
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (j < pend) old[j] = base[(size_t)S.jd[b][j] * M];
+            int jd[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) {
-                if (j < pend) {
+                jd[j] = S.jd[b][j];
+                if (j < pend && (unsigned)jd[j] < (unsigned)nd) old[j] = base[(size_t)jd[j] * M];
+            }
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (j < pend && (unsigned)jd[j] < (unsigned)nd) {
                     float s = 0.f;
 #pragma unroll
                     for (int w = 0; w < kWarps; ++w) s += S.red[b][j][w][lane];
-                    base[(size_t)S.jd[b][j] * M] = kahan_add(old[j], s);
+                    base[(size_t)jd[j] * M] = kahan_add(old[j], s);
                 }
             }
             __syncwarp();
@@ -634,12 +647,14 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
         cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        k_delay_f32_tiled<false><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.err);
+        k_delay_f32_tiled<false><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
+                                                               a.stall_group);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
-        k_delay_f32_tiled<true><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.err);
+        k_delay_f32_tiled<true><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
+                                                              a.stall_group);
     }
     return cudaGetLastError();
 }

@@ -62,6 +62,7 @@ struct nfs_ctx {
     int stage_frames = 1;
     int delay_variant = 0;
     int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
+    int stall_group = -1; // test hook of the bounded-wait path (NFS_OPT_TEST_STALL_GROUP)
     int device = 0;
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     std::vector<int32_t> delays;
@@ -331,6 +332,7 @@ int flush_block(nfs_ctx *c)
     a.sched = c->sched;
     a.err = c->d_err;
     a.tau_max = c->tau_max;
+    a.stall_group = c->stall_group;
     int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
                    "delay_f32");
     if (rc) return rc;
@@ -736,6 +738,10 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             if (v < 0 || v > 1) return NFS_EINVAL;
             c->fft_generic = (int)v;
             return NFS_OK;
+        case NFS_OPT_TEST_STALL_GROUP:
+            if (v < -1 || v > 1000000) return NFS_EINVAL;
+            c->stall_group = (int)v;
+            return NFS_OK;
         default: return NFS_EINVAL;
     }
 }
@@ -752,6 +758,7 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_FFT_CHUNK: *v = c->fft_chunk; return NFS_OK;
         case NFS_OPT_DELAY_VARIANT: *v = c->delay_variant; return NFS_OK;
         case NFS_OPT_FFT_GENERIC: *v = c->fft_generic; return NFS_OK;
+        case NFS_OPT_TEST_STALL_GROUP: *v = c->stall_group; return NFS_OK;
         default: return NFS_EINVAL;
     }
 }
@@ -779,5 +786,56 @@ int nfs_reset_timings(nfs_ctx *c)
 }
 
 int64_t nfs_launch_count(const nfs_ctx *c) { return c ? c->launches : -1; }
+
+int nfs_fit(nfs_ctx *c, const double *D_in, float *A, float *B, float *Gamma, int iters, int method)
+{
+    int rc = enter(c);
+    if (rc) return rc;
+    if (!A || !B || !Gamma || iters < 0 || (method != NFS_FIT_GAUSS_NEWTON && method != NFS_FIT_ADAM)) return NFS_EINVAL;
+    const int nd = c->nd, nq = c->nq;
+    std::vector<double> Dh;
+    std::vector<long long> pairs((size_t)nd);
+    if (D_in) {
+        for (int j = 0; j < nd; ++j) pairs[j] = std::max<long long>(0, c->nframes - c->delays[j]);
+    } else {
+        Dh.resize((size_t)nd * nq);
+        std::vector<int64_t> bc((size_t)nq), pc((size_t)nd);
+        if ((rc = nfs_structure_function(c, Dh.data(), bc.data(), pc.data(), nullptr))) return rc;
+        for (int j = 0; j < nd; ++j) pairs[j] = pc[j];
+        D_in = Dh.data();
+    }
+    // delays with pairs (a delay with none carries no data); tau = 0 carries no dynamics
+    std::vector<float> Df, tf;
+    for (int j = 0; j < nd; ++j) {
+        if (pairs[j] <= 0 || c->delays[j] == 0) continue;
+        tf.push_back((float)c->delays[j]);
+        for (int b = 0; b < nq; ++b) Df.push_back((float)D_in[(size_t)j * nq + b]);
+    }
+    const int nu = (int)tf.size();
+    if (nu == 0) return NFS_ESTATE;
+    float *dD = nullptr, *dt = nullptr, *dp = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&dD, sizeof(float) * Df.size(), c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dt, sizeof(float) * tf.size(), c->stream);
+    if (e == cudaSuccess) e = cudaMallocAsync((void **)&dp, sizeof(float) * 3 * (size_t)nq, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dD, Df.data(), sizeof(float) * Df.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp, A, sizeof(float) * nq, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp + nq, B, sizeof(float) * nq, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dp + 2 * nq, Gamma, sizeof(float) * nq, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        e = (method == NFS_FIT_GAUSS_NEWTON)
+                ? launch_fit_gauss_newton(dD, dt, nu, nq, dp, dp + nq, dp + 2 * nq, iters, 1e-3f, c->stream)
+                : launch_fit_adam(dD, dt, nu, nq, dp, dp + nq, dp + 2 * nq, iters, 1e-2f, c->stream);
+        if (e == cudaSuccess) c->launches++;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(A, dp, sizeof(float) * nq, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(B, dp + nq, sizeof(float) * nq, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(Gamma, dp + 2 * nq, sizeof(float) * nq, cudaMemcpyDeviceToHost, c->stream);
+    cudaFreeAsync(dD, c->stream);
+    cudaFreeAsync(dt, c->stream);
+    cudaFreeAsync(dp, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? c->err : set_cuda_error(c, e, "nfs_fit");
+}
 
 }  // extern "C"

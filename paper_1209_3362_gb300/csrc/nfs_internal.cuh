@@ -151,6 +151,7 @@ struct DelayArgs {
     const DelaySchedule *sched;  // host copy; NULL = no tiled schedule (one-thread-per-mode kernel)
     int *err;     // device status words (kDelayErrWords): [0] set when a bounded wait gives up, [1..] where
     int tau_max;
+    int stall_group;  // test hook: the producer stops before this copy group (-1: off)
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
 
@@ -167,5 +168,13 @@ cudaError_t launch_bin(const Acc *acc, size_t M, int nd, int nq, const int *bin_
 // 2-D export: out[ky][kx] (kx < Wh) = value_j(ky*Wp + kx) / pairs.
 template <typename Acc>
 cudaError_t launch_export(const Acc *acc_j, const Geometry &g, long long pairs, double *out, cudaStream_t s);
+
+// Eq. 1 fit (k_fit.cu); all pointers device, D [nd][nq], tau [nd], parameters [nq].
+cudaError_t launch_fit_loss_grad(const float *D, const float *tau, int nd, int nq, const float *A, const float *B,
+                                 const float *G, float *loss, float *gA, float *gB, float *gG, cudaStream_t s);
+cudaError_t launch_fit_gauss_newton(const float *D, const float *tau, int nd, int nq, float *A, float *B, float *G,
+                                    int iters, float lambda, cudaStream_t s);
+cudaError_t launch_fit_adam(const float *D, const float *tau, int nd, int nq, float *A, float *B, float *G, int iters,
+                            float lr, cudaStream_t s);
 
 }  // namespace nfs

@@ -236,7 +236,8 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
         NA_CK(launch_col_fft<float>(nf, g, pcol, twc, ring, R, slot0, s, scr, nullptr));
         done += nf;
         if (done - processed == kNaBlock || done == n_frames) {
-            DelayArgs a{ring, R, g.M, processed, (int)(done - processed), dd, nd, acc, nullptr, nullptr, delays[nd - 1]};
+            DelayArgs a{ring, R, g.M, processed, (int)(done - processed), dd, nd, acc, nullptr, nullptr, delays[nd - 1],
+                        -1};
             NA_CK(launch_delay_f32(a, 1, s));  // the one-thread-per-mode kernel: blocks of 32 frames
             processed = done;
         }
