@@ -205,7 +205,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS))
+    ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS) + sorted(S.RAGGED_WORKLOADS))
     ap.add_argument("--frames", type=int, default=0, help="override N (smaller runs; not a bench value)")
     ap.add_argument("--H", type=int, default=0, help="override frame height (profiling cases; not a bench value)")
     ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
@@ -217,6 +217,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     args = ap.parse_args()
+    if args.workload in S.RAGGED_WORKLOADS:
+        return run_ragged(args, S.RAGGED_WORKLOADS[args.workload])
     w = S.WORKLOADS[args.workload]
     if args.frames or args.H or args.W or args.delays:
         import dataclasses
@@ -403,6 +405,61 @@ def main():
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def run_ragged(args, rw):
+    """Ragged batch: every sequence's frames resident in HBM, one pass of all sequences per step
+    through nfs_batch_push_device (one persistent delay launch per frame block for all members)."""
+    import torch
+    import paper_1209_3362_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    P.build()
+    P.load_library()
+    mem = rw.members()
+    frames = []
+    for (H, W, Dc, d, nq, seed) in mem:
+        src = S.OUFrameSource(H, W, Dc, seed=seed, device="cuda", dtype=torch.float32)
+        f = torch.empty((rw.N, H, W), dtype=torch.int16, device="cuda")
+        for o in range(0, rw.N, 50):
+            f[o:o + 50] = src.next_frames(min(50, rw.N - o))
+        frames.append(f)
+    torch.cuda.synchronize()
+    b = P.NFSBatch([(m[0], m[1]) for m in mem], [m[3] for m in mem], [m[4] for m in mem])
+    stream = torch.cuda.ExternalStream(b.stream)
+
+    def step():
+        b.reset()
+        b.push_frames_device(frames)
+        return [b.structure_function(s) for s in range(len(mem))]
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    l0 = b.launch_count
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = max(ev0.elapsed_time(ev1), 1000.0 * wall) / args.steps
+    total = rw.n_seq * rw.N
+    shapes = {}
+    for m in mem:
+        shapes[f"{m[0]}x{m[1]}"] = shapes.get(f"{m[0]}x{m[1]}", 0) + 1
+    line = {"metric": f"frames/s, ragged batch of {rw.n_seq} sequences x {rw.N} frames (uneven shapes)",
+            "value": total / (step_ms / 1000.0), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": rw.name, "sequences": rw.n_seq, "frames_per_sequence": rw.N, "shapes": shapes,
+                       "delays": 64, "tau_max": rw.N // 2},
+            "gpu_launches": int(b.launch_count - l0), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    b.close()
 
 
 def ctx_bytes(w, K, M):

@@ -140,7 +140,8 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 #define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K (FP32) or tau_max + 64 (FP64) */
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
 #define NFS_OPT_PATH 5         /* read-only: NFS_PATH_* */
-#define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..64; default 4) */
+#define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..16 FP32, 1..64 FP64; default 4;
+                                  0 = choose by measurement, FP32 path) */
 #define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel: 0 = tiled, packed f32x2 math (default);
                                    1 = one thread per mode; 2 = tiled, scalar FP32 math */
 #define NFS_OPT_FFT_GENERIC 8   /* 1 = generic FFT kernels even where size-specialised ones exist */
@@ -172,6 +173,39 @@ int nfs_reset_timings(nfs_ctx *ctx);
  * Number of kernel launches the context has issued since creation (all stages, both paths).
  */
 int64_t nfs_launch_count(const nfs_ctx *ctx);
+
+/*
+ * ---------------------------------------------------------------- ragged batch
+ * Many independent sequences (regions of interest, cameras, experiments) of uneven frame shapes
+ * and delay lists analysed together: each member is a context of its own, all members share one
+ * stream, and the delay update of every member whose block of K frames is complete runs in ONE
+ * persistent launch over a ragged work list of (sequence, 32-mode tile) items.  The FFT launch
+ * size of each frame shape is chosen by a measuring autotuner when the batch is created.
+ */
+typedef struct nfs_batch nfs_batch;
+
+/*
+ * n_seq sequences; sequence s has frames H[s] x W[s] (as nfs_create), delays
+ * delays[delay_offsets[s] .. delay_offsets[s+1]) (strictly increasing) and n_qbins[s] bins.
+ * NFS_EUNSUPPORTED also for a delay list too long for the tiled kernel's schedule.
+ */
+int nfs_batch_create(int n_seq, const int *H, const int *W, const int32_t *delay_offsets, const int32_t *delays,
+                     const int *n_qbins, nfs_batch **out);
+void nfs_batch_destroy(nfs_batch *b);
+/* Append host frames to one sequence (as nfs_push_frames). */
+int nfs_batch_push(nfs_batch *b, int seq, const uint16_t *host_frames, int n_frames);
+/* Append device frames to every sequence at once: dev_frames[s] holds n_frames[s] frames. */
+int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const int *n_frames);
+/* Finish every member's pending frames and return sequence seq's result (as nfs_structure_function). */
+int nfs_batch_structure_function(nfs_batch *b, int seq, double *D, int64_t *bin_counts, int64_t *pair_counts,
+                                 double *q_mean);
+int nfs_batch_reset(nfs_batch *b);
+int nfs_batch_synchronize(nfs_batch *b);
+/* The member context of sequence seq (owned by the batch: do not destroy it). */
+nfs_ctx *nfs_batch_member(nfs_batch *b, int seq);
+void *nfs_batch_get_stream(const nfs_batch *b);
+int64_t nfs_batch_launch_count(const nfs_batch *b);
+const char *nfs_batch_last_error(const nfs_batch *b);
 
 /*
  * ---------------------------------------------------------------- Eq. 1 fit

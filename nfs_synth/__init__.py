@@ -222,6 +222,28 @@ def workload_source(w: Workload, device: str | torch.device = "cpu", dtype=None)
     return OUFrameSource(w.H, w.W, w.Dc, w.gamma0, eps=w.eps, seed=w.seed, device=device, dtype=dtype)
 
 
+@dataclasses.dataclass(frozen=True)
+class RaggedWorkload:
+    """Many independent sequences of uneven frame shapes (regions of interest or cameras)."""
+
+    name: str
+    n_seq: int
+    N: int  # frames per sequence
+    seed: int
+
+    def members(self):
+        """[(H, W, Dc, delays, n_qbins, seed)] per sequence: shapes drawn uniformly from the six
+        camera ROI shapes, D uniform in [0.1, 5] px^2/frame, 64 log delays 1..N/2, n_q = min(H, W)/2."""
+        rng = np.random.Generator(np.random.PCG64(self.seed))
+        shapes = ragged_shapes(self.n_seq, self.seed + 1)
+        Ds = rng.uniform(0.1, 5.0, self.n_seq)
+        d = tuple(log_delays(1, self.N // 2, 64))
+        return [(h, w, float(Ds[i]), d, min(h, w) // 2, self.seed + 100 + i) for i, (h, w) in enumerate(shapes)]
+
+
+RAGGED_WORKLOADS = {"ragged48": RaggedWorkload("ragged48", 48, 500, 12093367)}
+
+
 def ragged_shapes(n_seq: int, seed: int) -> Sequence[tuple]:
     """Frame shapes for a ragged batch, drawn uniformly from the six camera ROI shapes."""
     shapes = [(128, 128), (256, 256), (384, 512), (512, 512), (768, 1024), (1024, 1024)]

@@ -88,6 +88,17 @@ def load_library(path: Optional[str] = None):
         "nfs_launch_count": (I64, [V]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
         "nfs_fit": (I, [V, V, V, V, V, I, I]),
+        "nfs_batch_create": (I, [I, V, V, V, V, V, PP]),
+        "nfs_batch_destroy": (None, [V]),
+        "nfs_batch_push": (I, [V, I, V, I]),
+        "nfs_batch_push_device": (I, [V, V, V]),
+        "nfs_batch_structure_function": (I, [V, I, V, V, V, V]),
+        "nfs_batch_reset": (I, [V]),
+        "nfs_batch_synchronize": (I, [V]),
+        "nfs_batch_member": (V, [V, I]),
+        "nfs_batch_get_stream": (V, [V]),
+        "nfs_batch_launch_count": (I64, [V]),
+        "nfs_batch_last_error": (ctypes.c_char_p, [V]),
         "nfs_fit_loss_grad": (I, [V, V, I, I, V, V, V, V, V, V, V, V]),
         "nfs_fit_gauss_newton": (I, [V, V, I, I, V, V, V, I, ctypes.c_float, V]),
     }
@@ -270,3 +281,91 @@ def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) ->
     if rc != NFS_OK:
         raise NFSError(rc, "nfs_structure_function_noalloc")
     return dict(D=D, bin_counts=bc, pair_counts=pc)
+
+
+class NFSBatch:
+    """Ragged batch of sequences (nfs_batch_*): uneven frame shapes and delay lists, one persistent
+    delay-update launch per frame block for all members."""
+
+    def __init__(self, shapes, delays_per_seq, n_qbins):
+        self._L = load_library()
+        self.shapes = [(int(h), int(w)) for h, w in shapes]
+        n = len(self.shapes)
+        self.delays = [np.ascontiguousarray(np.asarray(d, np.int32)) for d in delays_per_seq]
+        self.n_qbins = [int(q) for q in n_qbins]
+        assert len(self.delays) == n and len(self.n_qbins) == n
+        H = np.array([h for h, _ in self.shapes], np.int32)
+        W = np.array([w for _, w in self.shapes], np.int32)
+        off = np.zeros(n + 1, np.int32)
+        off[1:] = np.cumsum([d.size for d in self.delays])
+        flat = np.ascontiguousarray(np.concatenate(self.delays).astype(np.int32))
+        nq = np.array(self.n_qbins, np.int32)
+        h = ctypes.c_void_p()
+        rc = self._L.nfs_batch_create(n, _ptr(H), _ptr(W), _ptr(off), _ptr(flat), _ptr(nq), ctypes.byref(h))
+        if rc != NFS_OK:
+            raise NFSError(rc, "nfs_batch_create")
+        self._h = h
+
+    def _check(self, rc, what):
+        if rc != NFS_OK:
+            raise NFSError(rc, what, (self._L.nfs_batch_last_error(self._h) or b"").decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.nfs_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def push_frames(self, seq, frames):
+        a = np.ascontiguousarray(frames, dtype=np.uint16)
+        self._check(self._L.nfs_batch_push(self._h, int(seq), _ptr(a), a.shape[0]), "nfs_batch_push")
+
+    def push_frames_device(self, tensors):
+        """tensors[s]: CUDA tensor [n_s, H_s, W_s] of 2-byte integers (or None for no frames)."""
+        n = len(self.shapes)
+        ptrs = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in tensors])
+        counts = np.array([(t.shape[0] if t is not None else 0) for t in tensors], np.int32)
+        self._check(self._L.nfs_batch_push_device(self._h, ptrs, _ptr(counts)), "nfs_batch_push_device")
+
+    def structure_function(self, seq):
+        nd, nq = self.delays[seq].size, self.n_qbins[seq]
+        D = np.zeros((nd, nq), np.float64)
+        bc = np.zeros(nq, np.int64)
+        pc = np.zeros(nd, np.int64)
+        qm = np.zeros(nq, np.float64)
+        self._check(self._L.nfs_batch_structure_function(self._h, int(seq), _ptr(D), _ptr(bc), _ptr(pc), _ptr(qm)),
+                    "nfs_batch_structure_function")
+        return dict(D=D, bin_counts=bc, pair_counts=pc, q_mean=qm)
+
+    def reset(self):
+        self._check(self._L.nfs_batch_reset(self._h), "nfs_batch_reset")
+
+    def synchronize(self):
+        self._check(self._L.nfs_batch_synchronize(self._h), "nfs_batch_synchronize")
+
+    @property
+    def stream(self) -> int:
+        return int(self._L.nfs_batch_get_stream(self._h) or 0)
+
+    @property
+    def launch_count(self) -> int:
+        return int(self._L.nfs_batch_launch_count(self._h))
+
+    def member_option(self, seq, key) -> int:
+        v = ctypes.c_int64()
+        c = self._L.nfs_batch_member(self._h, int(seq))
+        rc = self._L.nfs_get_option(c, int(key), ctypes.byref(v))
+        if rc != NFS_OK:
+            raise NFSError(rc, "nfs_get_option")
+        return int(v.value)

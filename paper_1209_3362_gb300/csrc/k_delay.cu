@@ -403,18 +403,22 @@ __device__ __forceinline__ void hand_over(TiledSmem &S, int b, int lane)
     }
 }
 
-template <bool PACKED>
-__global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
-                                                                 long long t0, int nb,
-                                                                 const __grid_constant__ DelaySchedule sched,
-                                                                 float2 *__restrict__ acc, int nd,
-                                                                 int *__restrict__ err, int stall_group)
+__device__ __forceinline__ void mbar_inval(unsigned long long *bar)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
-    const size_t tile = blockIdx.x;
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// One CTA's pass over one 32-mode tile for a block of new frames t0 .. t0+nb-1 (all warps of the
+// CTA take part; every role falls through to the final barrier, so a persistent caller can run
+// several tiles in a row).  sched: the sequence's schedule (kernel parameters or global memory);
+// nst, nbatch: its stages and batches for this block (early blocks leave late stages out).
+template <bool PACKED>
+__device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict__ ring, int R, size_t M,
+                                          long long t0, int nb, const DelaySchedule &sched, int nst, int nbatch,
+                                          float2 *__restrict__ acc, int nd, int *__restrict__ err, int stall_group,
+                                          size_t tile)
+{
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nst = sched.nst;
 
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_init(&S.full[b], 1);
@@ -432,7 +436,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    __syncthreads();  // the only CTA-wide barrier
+    __syncthreads();
 
     if (warp == kProducer) {
         // issue every copy group as soon as its rows are free and its barrier is reusable
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                 issued = g + 1;
             }
             if (*(volatile int *)&S.abort || *(volatile int *)err) {
-                // let copies still in flight land (bounded) before the CTA's shared memory goes away
+                // let copies still in flight land (bounded) before the shared memory is reused
                 for (int g = issued - 1; g >= 0 && g >= issued - kFullBars; --g) {
                     unsigned long long *bar = &S.full[g % kFullBars];
                     const unsigned par = (unsigned)((g / kFullBars) & 1);
@@ -483,12 +487,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                 }
             }
         }
-        return;
-    }
-
-    if (warp == kWriter) {
+    } else if (warp == kWriter) {
         // reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs
-        for (int k = 0; k < sched.nbatch; ++k) {
+        for (int k = 0; k < nbatch; ++k) {
             const int b = k & 1;
             // After a failed wait the batch may not be written yet: stop touching global memory
             // (the launch's results are void and the error word says so).
@@ -517,47 +518,122 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                 *(volatile int *)&S.wdrained = k + 1;
             }
         }
-        return;
-    }
-
-    // consumers
-    const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
-    const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
-    wait_group(S, 0, err);
-    pk_t xt[kTw];
+    } else {
+        // consumers
+        const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
+        const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
+        wait_group(S, 0, err);
+        pk_t xt[kTw];
 #pragma unroll
-    for (int i = 0; i < kTw; ++i) xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane]);
-    step_done(S, lane);
-
-    // After a failed wait the loop still runs to the end (every shared-memory index stays in bounds,
-    // the numbers are wrong and the error word says so), so no barrier ever loses a warp.
-    int pend = 0, batch = 0;
-    auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 2
-        if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err, 3, k);
-    };
-    open_batch(0);
-    for (int s = 0; s < nst; ++s) {
-        const Stage st = sched.st[s];
-        wait_group(S, s + 1, err);
-        for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
-            const SubRun sr = sched.sr[r];
-            if (pend + sr.len > 16) {
-                if (tid == 0) S.pend[batch & 1] = pend;
-                hand_over(S, batch & 1, lane);
-                ++batch;
-                pend = 0;
-                open_batch(batch);
-            }
-            if (tid < sr.len) S.jd[batch & 1][pend + tid] = sr.j0 + tid;
-            subrun_dispatch<PACKED>(S, xt, lane, warp, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim);
-            pend += sr.len;
-        }
+        for (int i = 0; i < kTw; ++i) xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane]);
         step_done(S, lane);
+
+        // After a failed wait the loop still runs to the end (every shared-memory index stays in
+        // bounds, the numbers are wrong and the error word says so), so no barrier loses a warp.
+        int pend = 0, batch = 0;
+        auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 2
+            if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err, 3, k);
+        };
+        open_batch(0);
+        for (int s = 0; s < nst; ++s) {
+            const Stage st = sched.st[s];
+            wait_group(S, s + 1, err);
+            for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
+                const SubRun sr = sched.sr[r];
+                if (pend + sr.len > 16) {
+                    if (tid == 0) S.pend[batch & 1] = pend;
+                    hand_over(S, batch & 1, lane);
+                    ++batch;
+                    pend = 0;
+                    open_batch(batch);
+                }
+                if (tid < sr.len) S.jd[batch & 1][pend + tid] = sr.j0 + tid;
+                subrun_dispatch<PACKED>(S, xt, lane, warp, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim);
+                pend += sr.len;
+            }
+            step_done(S, lane);
+        }
+        if (pend) {
+            if (tid == 0) S.pend[batch & 1] = pend;
+            hand_over(S, batch & 1, lane);
+        }
     }
-    if (pend) {
-        if (tid == 0) S.pend[batch & 1] = pend;
-        hand_over(S, batch & 1, lane);
+    __syncthreads();  // every role has finished this tile (all copies issued were consumed)
+    if (tid == 0) {
+        for (int b = 0; b < kFullBars; ++b) mbar_inval(&S.full[b]);
+        for (int b = 0; b < 2; ++b) {
+            mbar_inval(&S.red_full[b]);
+            mbar_inval(&S.red_free[b]);
+        }
     }
+    __syncthreads();
+}
+
+template <bool PACKED>
+__global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *__restrict__ ring, int R, size_t M,
+                                                                 long long t0, int nb,
+                                                                 const __grid_constant__ DelaySchedule sched,
+                                                                 float2 *__restrict__ acc, int nd,
+                                                                 int *__restrict__ err, int stall_group)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
+    tile_pass<PACKED>(S, ring, R, M, t0, nb, sched, sched.nst, sched.nbatch, acc, nd, err, stall_group, blockIdx.x);
+}
+
+// Ragged batch: one persistent launch over the tiles of several sequences (each with its own frame
+// shape, ring, accumulators and schedule); CTA b takes work items b, b + gridDim.x, ...
+template <bool PACKED>
+__global__ void __launch_bounds__(kThreads, 1) k_delay_f32_batched(const BatchItem *__restrict__ items, int nitems,
+                                                                   long long total_tiles, int *__restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
+    for (long long i = blockIdx.x; i < total_tiles; i += gridDim.x) {
+        int lo = 0, hi = nitems - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (items[mid].first <= i)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const BatchItem it = items[lo];
+        tile_pass<PACKED>(S, it.ring, it.R, it.M, it.t0, it.nb, *it.sched, it.nst, it.nbatch, it.acc, it.nd, err, -1,
+                          (size_t)(i - it.first));
+    }
+}
+
+cudaError_t launch_delay_batched(const BatchItem *d_items, int nitems, long long total_tiles, int *err, int n_sm,
+                                 cudaStream_t s)
+{
+    if (nitems <= 0 || total_tiles <= 0) return cudaSuccess;
+    const size_t smem = sizeof(TiledSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_delay_f32_batched<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    const long long grid = total_tiles < (long long)n_sm ? total_tiles : (long long)n_sm;
+    k_delay_f32_batched<true><<<(unsigned)grid, kThreads, smem, s>>>(d_items, nitems, total_tiles, err);
+    return cudaGetLastError();
+}
+
+// Stages and batches of a block whose last frame is tlast (stages whose smallest delay exceeds it
+// have no valid pair yet).
+void truncate_schedule(const DelaySchedule &sc, long long tlast, int *nst_out, int *nbatch_out)
+{
+    int nst = 0;
+    while (nst < sc.nst && (long long)sc.sr[sc.st[nst].sr0].d0 <= tlast) ++nst;
+    int nb_batches = 0, pend = 0;
+    if (nst > 0)
+        for (int r = 0; r < sc.st[nst - 1].sr0 + sc.st[nst - 1].nsr; ++r) {
+            if (pend + sc.sr[r].len > 16) {
+                ++nb_batches;
+                pend = 0;
+            }
+            pend += sc.sr[r].len;
+        }
+    *nst_out = nst;
+    *nbatch_out = nb_batches + (pend ? 1 : 0);
 }
 
 // ------------------------------------------------------------------ simple block kernel (variant 1)
@@ -625,22 +701,11 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
     // Stages whose smallest delay exceeds the block's last frame have no valid pair yet (early
     // blocks of a sequence): leave them out of this launch, with the batches they would fill.
     DelaySchedule sc = *a.sched;
-    const long long tlast = a.t0 + a.nb - 1;
-    int nst = 0;
-    while (nst < sc.nst && (long long)sc.sr[sc.st[nst].sr0].d0 <= tlast) ++nst;
+    int nst = 0, nbatch = 0;
+    truncate_schedule(sc, a.t0 + a.nb - 1, &nst, &nbatch);
     if (nst == 0) return cudaSuccess;  // nothing to add (or only tau = 0 in the list)
-    {
-        int nb_batches = 0, pend = 0;
-        for (int r = 0; r < sc.st[nst - 1].sr0 + sc.st[nst - 1].nsr; ++r) {
-            if (pend + sc.sr[r].len > 16) {
-                ++nb_batches;
-                pend = 0;
-            }
-            pend += sc.sr[r].len;
-        }
-        sc.nbatch = nb_batches + (pend ? 1 : 0);
-        sc.nst = nst;
-    }
+    sc.nst = nst;
+    sc.nbatch = nbatch;
     const size_t smem = sizeof(TiledSmem);
     const unsigned grid = (unsigned)(a.M / kTile);
     if (variant == 2) {

@@ -5,6 +5,8 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 
 #include "nfs_internal.cuh"
@@ -63,6 +65,8 @@ struct nfs_ctx {
     int delay_variant = 0;
     int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
     int stall_group = -1; // test hook of the bounded-wait path (NFS_OPT_TEST_STALL_GROUP)
+    bool own_streams = true;   // false for members of a batch (the batch owns the streams)
+    bool defer_delay = false;  // members of a batch: the batch runs the delay update of full blocks
     int device = 0;
     cudaStream_t stream = nullptr, copy_stream = nullptr;
     std::vector<int32_t> delays;
@@ -301,8 +305,10 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_export);
     delete c->sched;
     cudaFree(c->d_err);
-    if (c->stream) cudaStreamDestroy(c->stream);
-    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->own_streams) {
+        if (c->stream) cudaStreamDestroy(c->stream);
+        if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    }
 }
 
 int alloc_dev(nfs_ctx *c, void **p, size_t bytes)
@@ -367,7 +373,7 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
         }, "col_fft_f32");
         if (rc) return rc;
         c->nframes += nf;
-        if (c->nframes - c->nprocessed >= c->K) return flush_block(c);
+        if (c->nframes - c->nprocessed >= c->K && !c->defer_delay) return flush_block(c);
         return NFS_OK;
     }
     rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
@@ -393,6 +399,62 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
     if (c->timing && c->pending.size() > 200000) return harvest(c);
     return NFS_OK;
 }
+
+// FFT launch-pair size (frames per row/column launch) chosen by measurement per frame shape:
+// candidates 1, 2, 4, 8, 16 each transform 16 zero frames from the staging ring; the fastest is
+// kept for the process (a context's first transform of a shape pays for the measurement).
+int autotune_fft_chunk(nfs_ctx *c)
+{
+    static std::mutex mu;
+    static std::map<std::pair<int, int>, int> cache;
+    const std::pair<int, int> key(c->g.H, c->g.W);
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            c->fft_chunk = it->second;
+            return NFS_OK;
+        }
+    }
+    const int nfr = 16;
+    const int cands[5] = {1, 2, 4, 8, 16};
+    CK(c, cudaMemsetAsync(c->d_sums, 0, sizeof(unsigned long long) * kMaxChunk, c->stream));
+    CK(c, cudaMemsetAsync(c->d_ref, 0, sizeof(float) * c->g.HW, c->stream));
+    CK(c, cudaMemsetAsync(c->d_stage, 0, c->frame_bytes() * nfr, c->stream));
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    int best = c->fft_chunk;
+    float best_ms = 1e30f;
+    for (int rep = 0; rep < 2; ++rep)  // the first round warms up
+        for (int cand : cands) {
+            CK(c, cudaEventRecord(e0, c->stream));
+            for (int o = 0; o < nfr; o += cand) {
+                if (launch_row_fft<float>(c->d_stage + (size_t)o * c->g.HW, cand, c->d_sums, c->d_ref, c->g, c->plan_row,
+                                          (const float2 *)c->d_tw_row, (const float2 *)c->d_tw_post, (float2 *)c->d_ring,
+                                          c->R, o, c->stream, c->d_scratch, c->d_tws_row) != cudaSuccess ||
+                    launch_col_fft<float>(cand, c->g, c->plan_col, (const float2 *)c->d_tw_col, (float2 *)c->d_ring, c->R,
+                                          o, c->stream, c->d_scratch, c->d_tws_col) != cudaSuccess)
+                    return set_cuda_error(c, cudaGetLastError(), "autotune");
+                c->launches += 2;
+            }
+            CK(c, cudaEventRecord(e1, c->stream));
+            CK(c, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(c, cudaEventElapsedTime(&ms, e0, e1));
+            if (rep == 1 && ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->fft_chunk = best;
+    std::lock_guard<std::mutex> lock(mu);
+    cache[key] = best;
+    return NFS_OK;
+}
+
 
 // Frames the next chunk may take so that a chunk never spans two delay blocks.
 int next_chunk(const nfs_ctx *c, long long remaining, int cap)
@@ -727,6 +789,7 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
     switch (key) {
         case NFS_OPT_TIMING: c->timing = v != 0; return NFS_OK;
         case NFS_OPT_FFT_CHUNK:
+            if (v == 0 && c->f32()) return autotune_fft_chunk(c);
             if (v < 1 || v > (c->f32() ? kMaxChunkF32 : kMaxChunk)) return NFS_EINVAL;
             c->fft_chunk = (int)v;
             return NFS_OK;
@@ -837,5 +900,262 @@ int nfs_fit(nfs_ctx *c, const double *D_in, float *A, float *B, float *Gamma, in
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     return e == cudaSuccess ? c->err : set_cuda_error(c, e, "nfs_fit");
 }
+
+// ---------------------------------------------------------------- ragged batch
+
+struct nfs_batch {
+    int n = 0, device = 0, n_sm = 0;
+    std::vector<nfs_ctx *> seq;
+    cudaStream_t stream = nullptr, copy_stream = nullptr;
+    DelaySchedule *d_scheds = nullptr;  // one per sequence
+    BatchItem *d_items = nullptr;       // work list of one launch
+    int *d_err = nullptr;
+    std::vector<BatchItem> items;
+    int err = NFS_OK;
+    std::string errmsg;
+    long long launches = 0;
+};
+
+static void batch_free(nfs_batch *b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);
+    for (nfs_ctx *c : b->seq) nfs_destroy(c);
+    cudaFree(b->d_scheds);
+    cudaFree(b->d_items);
+    cudaFree(b->d_err);
+    if (b->stream) cudaStreamDestroy(b->stream);
+    if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
+    delete b;
+}
+
+static int batch_fail(nfs_batch *b, cudaError_t e, const char *where)
+{
+    if (e == cudaSuccess) return NFS_OK;
+    b->errmsg = std::string(where) + ": " + cudaGetErrorString(e);
+    if (b->err == NFS_OK) b->err = NFS_ECUDA;
+    return NFS_ECUDA;
+}
+
+// One persistent launch over every member whose pending block is full (all = false) or non-empty
+// (all = true).
+static int batch_flush(nfs_batch *b, bool all)
+{
+    b->items.clear();
+    long long total = 0;
+    for (size_t s = 0; s < b->seq.size(); ++s) {
+        nfs_ctx *c = b->seq[s];
+        const long long pend = c->nframes - c->nprocessed;
+        if (pend <= 0 || (!all && pend < c->K)) continue;
+        int nst = 0, nbatch = 0;
+        truncate_schedule(*c->sched, c->nframes - 1, &nst, &nbatch);
+        if (nst > 0) {
+            BatchItem it;
+            it.ring = (const float2 *)c->d_ring;
+            it.acc = (float2 *)c->d_acc;
+            it.sched = b->d_scheds + s;
+            it.t0 = c->nprocessed;
+            it.first = total;
+            it.M = c->g.M;
+            it.R = c->R;
+            it.nb = (int)pend;
+            it.nd = c->nd;
+            it.nst = nst;
+            it.nbatch = nbatch;
+            b->items.push_back(it);
+            total += (long long)(c->g.M / kTile);
+        }
+        c->nprocessed = c->nframes;
+    }
+    if (b->items.empty()) return NFS_OK;
+    cudaError_t e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * b->items.size(),
+                                    cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = launch_delay_batched(b->d_items, (int)b->items.size(), total, b->d_err, b->n_sm, b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "batched delay update");
+    b->launches++;
+    return NFS_OK;
+}
+
+static int batch_enter(nfs_batch *b)
+{
+    if (!b) return NFS_EINVAL;
+    cudaError_t e = cudaSetDevice(b->device);
+    if (e != cudaSuccess) return batch_fail(b, e, "cudaSetDevice");
+    return b->err;
+}
+
+// the device status of the batched launches (after a synchronisation)
+static int batch_check(nfs_batch *b)
+{
+    int dev_err[kDelayErrWords] = {};
+    cudaError_t e = cudaMemcpyAsync(dev_err, b->d_err, sizeof(dev_err), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return batch_fail(b, e, "batch status");
+    if (dev_err[0]) {
+        char buf[160];
+        snprintf(buf, sizeof(buf), "batched delay kernel: a bounded wait gave up (kind %d, cta %d, warp %d, index %d)",
+                 dev_err[1], dev_err[2], dev_err[3], dev_err[4]);
+        b->errmsg = buf;
+        if (b->err == NFS_OK) b->err = NFS_ETIMEOUT;
+    }
+    return b->err;
+}
+
+int nfs_batch_create(int n_seq, const int *H, const int *W, const int32_t *delay_offsets, const int32_t *delays,
+                     const int *n_qbins, nfs_batch **out)
+{
+    if (!out) return NFS_EINVAL;
+    *out = nullptr;
+    if (n_seq <= 0 || !H || !W || !delay_offsets || !delays || !n_qbins) return NFS_EINVAL;
+    for (int s = 0; s < n_seq; ++s)
+        if (delay_offsets[s + 1] <= delay_offsets[s]) return NFS_EINVAL;
+    nfs_batch *b = new (std::nothrow) nfs_batch();
+    if (!b) return NFS_ENOMEM;
+    cudaGetDevice(&b->device);
+    b->n = n_seq;
+    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        batch_free(b);
+        return NFS_ECUDA;
+    }
+    std::vector<DelaySchedule> scheds((size_t)n_seq);
+    for (int s = 0; s < n_seq; ++s) {
+        nfs_ctx *c = nullptr;
+        const int rc = create_impl(H[s], W[s], delays + delay_offsets[s], delay_offsets[s + 1] - delay_offsets[s],
+                                   n_qbins[s], NFS_PATH_FUSED_F32, 0, &c);
+        if (rc) {
+            batch_free(b);
+            return rc;
+        }
+        b->seq.push_back(c);
+        if (!c->sched) {  // delay list too long for the tiled kernel's schedule
+            batch_free(b);
+            return NFS_EUNSUPPORTED;
+        }
+        cudaStreamSynchronize(c->stream);
+        cudaStreamDestroy(c->stream);
+        cudaStreamDestroy(c->copy_stream);
+        c->stream = b->stream;
+        c->copy_stream = b->copy_stream;
+        c->own_streams = false;
+        c->defer_delay = true;
+        scheds[s] = *c->sched;
+        if (autotune_fft_chunk(c)) {
+            batch_free(b);
+            return NFS_ECUDA;
+        }
+    }
+    if (cudaMalloc(&b->d_scheds, sizeof(DelaySchedule) * (size_t)n_seq) != cudaSuccess ||
+        cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n_seq) != cudaSuccess ||
+        cudaMalloc(&b->d_err, sizeof(int) * kDelayErrWords) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return NFS_ENOMEM;
+    }
+    if (cudaMemcpy(b->d_scheds, scheds.data(), sizeof(DelaySchedule) * (size_t)n_seq, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemset(b->d_err, 0, sizeof(int) * kDelayErrWords) != cudaSuccess) {
+        batch_free(b);
+        return NFS_ECUDA;
+    }
+    *out = b;
+    return NFS_OK;
+}
+
+void nfs_batch_destroy(nfs_batch *b) { batch_free(b); }
+
+int nfs_batch_push(nfs_batch *b, int seq, const uint16_t *host_frames, int n)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    if (seq < 0 || seq >= b->n || n < 0 || (n > 0 && !host_frames)) return NFS_EINVAL;
+    nfs_ctx *c = b->seq[seq];
+    long long done = 0;
+    while (done < n) {
+        const long long room = c->K - (c->nframes - c->nprocessed);
+        if (room <= 0) {
+            if ((rc = batch_flush(b, false))) return rc;
+            continue;
+        }
+        const int m = (int)std::min<long long>(room, n - done);
+        if ((rc = nfs_push_frames(c, host_frames + (size_t)done * c->g.HW, m))) return rc;
+        done += m;
+    }
+    return b->err;
+}
+
+int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const int *n_frames)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    if (!dev_frames || !n_frames) return NFS_EINVAL;
+    std::vector<long long> done((size_t)b->n, 0);
+    for (int s = 0; s < b->n; ++s)
+        if (n_frames[s] < 0 || (n_frames[s] > 0 && !dev_frames[s])) return NFS_EINVAL;
+    for (;;) {
+        bool left = false, moved = false;
+        for (int s = 0; s < b->n; ++s) {
+            nfs_ctx *c = b->seq[s];
+            const long long rem = n_frames[s] - done[s];
+            if (rem <= 0) continue;
+            left = true;
+            const long long room = c->K - (c->nframes - c->nprocessed);
+            if (room <= 0) continue;
+            const int m = (int)std::min(room, rem);
+            if ((rc = nfs_push_frames_device(c, dev_frames[s] + (size_t)done[s] * c->g.HW, m))) return rc;
+            done[s] += m;
+            moved = true;
+        }
+        if (!left) break;
+        (void)moved;
+        // every member that still has frames now holds a full block: one launch for all of them
+        if ((rc = batch_flush(b, false))) return rc;
+    }
+    return b->err;
+}
+
+int nfs_batch_structure_function(nfs_batch *b, int seq, double *D, int64_t *bin_counts, int64_t *pair_counts,
+                                 double *q_mean)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    if (seq < 0 || seq >= b->n) return NFS_EINVAL;
+    if ((rc = batch_flush(b, true))) return rc;
+    if ((rc = batch_check(b))) return rc;
+    return nfs_structure_function(b->seq[seq], D, bin_counts, pair_counts, q_mean);
+}
+
+int nfs_batch_reset(nfs_batch *b)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    for (nfs_ctx *c : b->seq)
+        if ((rc = nfs_reset(c))) return rc;
+    return NFS_OK;
+}
+
+int nfs_batch_synchronize(nfs_batch *b)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    return batch_check(b);
+}
+
+nfs_ctx *nfs_batch_member(nfs_batch *b, int seq) { return (b && seq >= 0 && seq < b->n) ? b->seq[seq] : nullptr; }
+
+void *nfs_batch_get_stream(const nfs_batch *b) { return b ? (void *)b->stream : nullptr; }
+
+int64_t nfs_batch_launch_count(const nfs_batch *b)
+{
+    if (!b) return -1;
+    long long n = b->launches;
+    for (nfs_ctx *c : b->seq) n += c->launches;
+    return n;
+}
+
+const char *nfs_batch_last_error(const nfs_batch *b) { return b ? b->errmsg.c_str() : ""; }
 
 }  // extern "C"

@@ -155,6 +155,21 @@ struct DelayArgs {
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
 
+// One work item of the ragged batch: the block t0 .. t0+nb-1 of one sequence, tiles
+// first .. first+M/32-1 of the launch.
+struct BatchItem {
+    const float2 *ring;
+    float2 *acc;
+    const DelaySchedule *sched;  // device copy
+    long long t0;
+    long long first;
+    size_t M;
+    int R, nb, nd, nst, nbatch;
+};
+void truncate_schedule(const DelaySchedule &sc, long long tlast, int *nst, int *nbatch);
+cudaError_t launch_delay_batched(const BatchItem *d_items, int nitems, long long total_tiles, int *err, int n_sm,
+                                 cudaStream_t s);
+
 // Plain FP64 update of one frame t.
 cudaError_t launch_delay_f64(const double2 *ring, int R, size_t M, long long t, const int *delays, int nd,
                              double *acc, cudaStream_t s);
