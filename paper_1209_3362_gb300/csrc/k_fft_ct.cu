@@ -3,9 +3,10 @@
 // the real-to-complex split, then columns).
 //
 // With the transform length, radices and batch known at compile time every index is a shift or
-// a constant multiply and every per-thread loop unrolls.  Twiddles come from a per-stage table in
-// which consecutive butterflies read consecutive entries; shared memory is padded by one element
-// in 16 so the strided stores of the early Stockham stages do not collide in banks.  The row pass
+// a constant multiply and every per-thread loop unrolls.  Twiddles come from a per-stage table
+// with one row per twiddle power, in which consecutive butterflies read consecutive entries (a
+// warp's load is one contiguous run); shared memory is padded by one element in 16 so the
+// strided stores of the early Stockham stages do not collide in banks.  The row pass
 // writes the column-pair scratch, which the column pass reads as one contiguous run per CTA; the
 // column pass (in place in one buffer) writes each column as whole 32-mode tile rows of the ring.
 #include <cmath>
@@ -80,17 +81,76 @@ struct Dft<8> {
     }
 };
 
-// Radix of the next stage given the remaining length (also used on the host for the tables).
-__host__ __device__ constexpr int pick_radix(int rem)
+template <>
+struct Dft<16> {
+    // 16 = 4 x 4: transforms of length 4 over the inputs n = 4 n1 + n2 (for each n2), twiddles
+    // exp(-2 pi i n2 k1 / 16), transforms of length 4 over n2; output k1 + 4 k2
+    __device__ __forceinline__ static void run(float2 *v)
+    {
+        float2 y[4][4];
+#pragma unroll
+        for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+            for (int n1 = 0; n1 < 4; ++n1) y[n2][n1] = v[4 * n1 + n2];
+            Dft<4>::run(y[n2]);
+        }
+        const float c1 = 0.92387953251128675613f, s1 = 0.38268343236508977173f;  // cos, sin (pi / 8)
+        const float h = 0.70710678118654752440f;
+        // n2 = 1: powers 0, 1, 2, 3; n2 = 2: powers 0, 2, 4, 6; n2 = 3: powers 0, 3, 6, 9
+        y[1][1] = cmul(y[1][1], {c1, -s1});
+        y[1][2] = cmul(y[1][2], {h, -h});
+        y[1][3] = cmul(y[1][3], {s1, -c1});
+        y[2][1] = cmul(y[2][1], {h, -h});
+        y[2][2] = cmi(y[2][2]);
+        y[2][3] = cmul(y[2][3], {-h, -h});
+        y[3][1] = cmul(y[3][1], {s1, -c1});
+        y[3][2] = cmul(y[3][2], {-h, -h});
+        y[3][3] = cmul(y[3][3], {-c1, s1});
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) {
+            float2 z[4] = {y[0][k1], y[1][k1], y[2][k1], y[3][k1]};
+            Dft<4>::run(z);
+#pragma unroll
+            for (int k2 = 0; k2 < 4; ++k2) v[k1 + 4 * k2] = z[k2];
+        }
+    }
+};
+
+// Stockham stages left for a remaining length (radices 16, 8, 4, 3, 2), by dynamic programming
+// over the lengths up to rem (rem <= kMaxPlan; longer lengths take radix 8/4/2/3 greedily).
+constexpr int kMaxPlan = 2048;
+__host__ __device__ constexpr int radix_choice(int i) { return i == 0 ? 8 : (i == 1 ? 16 : (i == 2 ? 4 : (i == 3 ? 2 : 3))); }
+__host__ __device__ constexpr int n_stages(int rem)
 {
-    return (rem % 8 == 0 && rem != 16) ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3));
+    if (rem <= 1) return 0;
+    if (rem > kMaxPlan) return 1 << 20;
+    int dp[kMaxPlan + 1] = {};
+    for (int n = 2; n <= rem; ++n) {
+        int best = 1 << 20;
+        for (int i = 0; i < 5; ++i)
+            if (n % radix_choice(i) == 0 && 1 + dp[n / radix_choice(i)] < best) best = 1 + dp[n / radix_choice(i)];
+        dp[n] = best;
+    }
+    return dp[rem];
+}
+// Radix of the next stage of a length-L transform given the remaining length (also used on the
+// host for the tables).  Transforms of 2048 points and more take the fewest stages (each one a
+// round trip through shared memory; radix 16 pays off there), shorter ones radix 8 first (radix-16
+// butterflies leave threads idle in their CTAs and measured slower).
+__host__ __device__ constexpr int pick_radix(int L, int rem)
+{
+    if (L < 2048 || rem > kMaxPlan) return (rem % 8 == 0 && rem != 16) ? 8 : (rem % 4 == 0 ? 4 : (rem % 2 == 0 ? 2 : 3));
+    const int best = n_stages(rem);
+    for (int i = 0; i < 5; ++i)
+        if (rem % radix_choice(i) == 0 && 1 + n_stages(rem / radix_choice(i)) == best) return radix_choice(i);
+    return 2;
 }
 // Offset of the stage with sub-length NS in the per-stage twiddle table of length L.
 __host__ __device__ constexpr int tw_offset(int L, int NS)
 {
     int off = 0, ns = 1;
     while (ns < NS) {
-        const int r = pick_radix(L / ns);
+        const int r = pick_radix(L, L / ns);
         off += ns * (r - 1);
         ns *= r;
     }
@@ -139,7 +199,7 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
             const int k = j % NS;
             if (NS > 1) {
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tws + OFF + k * (R - 1) + (r - 1)));
+                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tws + OFF + (r - 1) * NS + k));
             }
             Dft<R>::run(v[p]);
             const int base = (j / NS) * NS * R + k;
@@ -158,7 +218,7 @@ __device__ __forceinline__ float2 *run_stages(float2 *a, float2 *b, const float2
     if constexpr (NS >= L) {
         return a;
     } else {
-        constexpr int R = pick_radix(L / NS);
+        constexpr int R = pick_radix(L, L / NS);
         stage<L, R, NS, NB, BFAST, INPLACE, NT>(a, INPLACE ? a : b, tws);
         __syncthreads();
         if constexpr (INPLACE)
@@ -297,9 +357,9 @@ std::vector<double> ct_stage_twiddles(int L)
     std::vector<double> t;
     int ns = 1;
     while (ns < L) {
-        const int r = ct::pick_radix(L / ns);
-        for (int k = 0; k < ns; ++k)
-            for (int q = 1; q < r; ++q) {
+        const int r = ct::pick_radix(L, L / ns);
+        for (int q = 1; q < r; ++q)  // q-major: consecutive butterflies k read consecutive entries
+            for (int k = 0; k < ns; ++k) {
                 const double a = 2.0 * M_PI * (double)k * q / ((double)ns * r);
                 t.push_back(std::cos(a));
                 t.push_back(-std::sin(a));

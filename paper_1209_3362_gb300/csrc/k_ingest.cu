@@ -18,13 +18,19 @@ __global__ void __launch_bounds__(256) k_frame_sums(const uint16_t *__restrict__
     size_t done = 0;
     if (VEC) {
         const uint4 *v = reinterpret_cast<const uint4 *>(f);
-        size_t n8 = HW / 8;
-        for (size_t i = tid; i < n8; i += nthr) {
-            uint4 q = __ldg(v + i);
-            unsigned int s = (q.x & 0xffffu) + (q.x >> 16) + (q.y & 0xffffu) + (q.y >> 16) + (q.z & 0xffffu) +
-                             (q.z >> 16) + (q.w & 0xffffu) + (q.w >> 16);
-            acc += s;
+        const size_t n8 = HW / 8;
+        auto sum8 = [](uint4 q) -> unsigned {
+            return (q.x & 0xffffu) + (q.x >> 16) + (q.y & 0xffffu) + (q.y >> 16) + (q.z & 0xffffu) + (q.z >> 16) +
+                   (q.w & 0xffffu) + (q.w >> 16);
+        };
+        size_t i = tid;
+        // four independent 16-byte loads in flight per thread
+        for (; i + 3 * nthr < n8; i += 4 * nthr) {
+            const uint4 q0 = __ldg(v + i), q1 = __ldg(v + i + nthr), q2 = __ldg(v + i + 2 * nthr),
+                        q3 = __ldg(v + i + 3 * nthr);
+            acc += (unsigned long long)(sum8(q0) + sum8(q1)) + (unsigned long long)(sum8(q2) + sum8(q3));
         }
+        for (; i < n8; i += nthr) acc += sum8(__ldg(v + i));
         done = n8 * 8;
     }
     for (size_t i = done + tid; i < HW; i += nthr) acc += f[i];
