@@ -243,3 +243,40 @@ def test_specialised_and_generic_fft_agree_at_2048(oracle_lib):
         check_counts(out[-1], ref)
         assert rel_err(out[-1], ref) <= TOL_F32, generic
     np.testing.assert_allclose(out[0]["D"], out[1]["D"], rtol=2e-6, atol=0)
+
+
+def test_full_size_2048_sampled_modes(oracle_lib):
+    """2048x2048 frames in the launch configuration the benchmark times (256-frame blocks, 4-frame
+    FFT launches, steady-state blocks after tau_max): sampled modes of the exported 2-D spectra
+    against the oracle's one-mode definition (real-space differences, one DFT coefficient), and
+    the binned D against an FP64 re-binning of the exported spectra with the oracle's bin table."""
+    H = W = 2048
+    nq = 1024
+    N = 560
+    delays = [1, 2, 3, 4, 17, 180, 300]
+    fr = S.OUFrameSource(H, W, 1.0, gamma0=0.01, seed=81, device="cuda", dtype=torch.float32).frames_numpy(N)
+    with P.NFS(H, W, delays, nq) as ctx:
+        assert ctx.get_option(P.OPT_BLOCK_FRAMES) == 256 and ctx.get_option(P.OPT_FFT_CHUNK) == 4
+        ctx.push_frames_device(torch.from_numpy(fr.view(np.int16)).cuda())
+        got = ctx.structure_function()
+        spectra = {j: ctx.export_spectrum(j) for j in (0, 1, 4, 6)}
+    # the oracle, one mode at a time: low and high q, the k_x = 0 and k_x = W/2 columns, k_y > H/2
+    samples = [(0, 3, 1), (5, 0, 4), (700, 1900, 6), (1024, 17, 0), (31, 1040, 4), (2, 2, 6)]
+    for kx, ky, j in samples:
+        ref = oracle_lib.mode_power(fr, kx, ky, delays[j])
+        v = spectra[j][ky, kx]
+        scale = float(np.mean(spectra[j]))
+        assert abs(v - ref) / (abs(ref) + 1e-3 * scale) <= 1e-4, (kx, ky, delays[j], v, ref)
+    # binning of the exported spectra (FP64, the oracle's integer bin rule and weights)
+    b_of, counts, _ = oracle_lib.bins(H, W, nq)
+    np.testing.assert_array_equal(got["bin_counts"], counts)
+    w = np.full((H, W // 2 + 1), 2.0)
+    w[:, 0] = 1.0
+    w[:, W // 2] = 1.0
+    keep = b_of >= 0
+    for j, D2 in spectra.items():
+        sums = np.bincount(b_of[keep], weights=(w * D2)[keep], minlength=nq)
+        Db = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
+        np.testing.assert_allclose(got["D"][j], Db, rtol=1e-12, atol=0)
+    assert np.all(got["pair_counts"] == [N - d for d in delays])
+    assert np.all(got["D"] >= 0.0)
