@@ -238,6 +238,45 @@ int nfs_fit_gauss_newton(const float *D, const float *tau, int n_delays, int n_b
                          float *Gamma, int iters, float lambda, void *stream);
 
 /*
+ * ---------------------------------------------------------------- out-of-core bands
+ * The processing paragraph's case of a sequence whose spectra do not fit in device memory: the
+ * memory holds only part of them and the frames are transferred to the GPU several times (the
+ * paper re-uploads images through a FIFO, diagonal by diagonal).  Here the delays are split into
+ * bands that each fit a budget of max_ring_slots spectra, and every band is one pass over the
+ * frames, which stay in host memory:
+ *   - band 0: an ordinary pass over the delays d with d + 256 <= max_ring_slots (one transform per
+ *     frame);
+ *   - a later band with smallest delay lo: a pass with shift s = 256 floor(lo / 256) that pairs
+ *     frame u + s (as the newer frame) with frame u + s - d, holding the frames u + s in a
+ *     256-slot ring and the frames u in a ring of (largest d - s) + 256 slots (two transforms per
+ *     frame index: N - s each); its delays d satisfy (d - s) + 512 <= max_ring_slots.
+ * Every pair is added in the same 256-frame block and in the same order as in one in-core pass,
+ * so the results equal those of nfs_create + nfs_push_frames + nfs_structure_function.
+ *
+ * nfs_out_of_core_plan() gives the bands without touching the GPU (host logic only):
+ *   band_first   [n_bands + 1] index of every band's first delay, then n_delays (may be NULL)
+ *   band_shift   [n_bands] the shift s of every band (0 for band 0) (may be NULL)
+ *   n_bands, n_transforms   out: the number of bands and of frame transforms all passes make
+ *                (N per ordinary band, 2 (N - s) per shifted band; the paper's FIFO scheme makes
+ *                N (2 alpha - 3 + 2 / alpha) for N - 1 = alpha N* frames and a memory of N*)
+ * Arrays sized for n_delays bands suffice.  NFS_EINVAL for budgets below 768 slots (a band must
+ * hold its first delay) or bad delays; NFS_EUNSUPPORTED if one delay alone exceeds the schedule.
+ *
+ * nfs_structure_function_out_of_core() runs the bands and returns, for the whole delay list, what
+ * nfs_structure_function returns (FP32 fused path).  frames: HOST memory [n_frames][H][W] uint16
+ * (pinned or pageable), read n_bands (or twice as many) times, not kept after the call.  The
+ * device memory a band holds (its rings, accumulators, staging) is freed before the next band.
+ * n_transforms (may be NULL) receives the frame transforms made.  Errors as nfs_create and
+ * nfs_structure_function; NFS_ESTATE if the passes did not transform the planned frames.
+ */
+int nfs_out_of_core_plan(const int32_t *delays, int n_delays, int64_t n_frames, int64_t max_ring_slots,
+                         int32_t *band_first, int64_t *band_shift, int *n_bands, int64_t *n_transforms);
+int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int n_delays, int n_qbins,
+                                       const uint16_t *frames, int64_t n_frames, int64_t max_ring_slots, double *D,
+                                       int64_t *bin_counts, int64_t *pair_counts, double *q_mean,
+                                       int64_t *n_transforms);
+
+/*
  * ---------------------------------------------------------------- analysis without allocation
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
  * device memory while they run: a process whose device memory is owned by another allocator

@@ -87,6 +87,8 @@ def load_library(path: Optional[str] = None):
         "nfs_reset_timings": (I, [V]),
         "nfs_launch_count": (I64, [V]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
+        "nfs_out_of_core_plan": (I, [V, I, I64, I64, V, V, ctypes.POINTER(I), ctypes.POINTER(I64)]),
+        "nfs_structure_function_out_of_core": (I, [I, I, V, I, I, V, I64, I64, V, V, V, V, ctypes.POINTER(I64)]),
         "nfs_fit": (I, [V, V, V, V, V, I, I]),
         "nfs_batch_create": (I, [I, V, V, V, V, V, PP]),
         "nfs_batch_destroy": (None, [V]),
@@ -281,6 +283,43 @@ def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) ->
     if rc != NFS_OK:
         raise NFSError(rc, "nfs_structure_function_noalloc")
     return dict(D=D, bin_counts=bc, pair_counts=pc)
+
+
+def out_of_core_plan(delays, n_frames: int, max_ring_slots: int) -> dict:
+    """Bands of the out-of-core mode (host logic only; see nfs_out_of_core_plan)."""
+    L = load_library()
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    first = np.zeros(d.size + 1, np.int32)
+    shift = np.zeros(d.size, np.int64)
+    nb = ctypes.c_int(0)
+    nt = ctypes.c_int64(0)
+    rc = L.nfs_out_of_core_plan(_ptr(d), int(d.size), int(n_frames), int(max_ring_slots), _ptr(first), _ptr(shift),
+                                ctypes.byref(nb), ctypes.byref(nt))
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_out_of_core_plan")
+    n = nb.value
+    return dict(band_first=first[:n + 1].copy(), band_shift=shift[:n].copy(), n_transforms=nt.value)
+
+
+def structure_function_out_of_core(frames, delays, n_qbins: int, max_ring_slots: int) -> dict:
+    """Binned D of host frames [N, H, W] uint16 with at most max_ring_slots spectra on the device
+    (bands of delays, each a pass over the frames; see nfs_structure_function_out_of_core)."""
+    L = load_library()
+    a = np.ascontiguousarray(frames.numpy() if hasattr(frames, "numpy") else frames)
+    a = a.view(np.uint16) if a.dtype == np.int16 else a.astype(np.uint16, copy=False)
+    N, H, W = a.shape
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    D = np.zeros((d.size, int(n_qbins)), np.float64)
+    bc = np.zeros(int(n_qbins), np.int64)
+    pc = np.zeros(d.size, np.int64)
+    qm = np.zeros(int(n_qbins), np.float64)
+    nt = ctypes.c_int64(0)
+    rc = L.nfs_structure_function_out_of_core(int(H), int(W), _ptr(d), int(d.size), int(n_qbins), _ptr(a), int(N),
+                                              int(max_ring_slots), _ptr(D), _ptr(bc), _ptr(pc), _ptr(qm),
+                                              ctypes.byref(nt))
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_structure_function_out_of_core")
+    return dict(D=D, bin_counts=bc, pair_counts=pc, q_mean=qm, n_transforms=nt.value)
 
 
 class NFSBatch:

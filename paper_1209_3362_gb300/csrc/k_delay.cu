@@ -37,12 +37,14 @@ __device__ __forceinline__ float2 kahan_add(float2 a, float p)
 
 // ------------------------------------------------------------------ schedule (host)
 
-bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, std::vector<Stage> *sts)
+bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *srs, std::vector<Stage> *sts)
 {
     srs->clear();
     sts->clear();
     int j = 0;
-    while (j < nd && delays[j] == 0) ++j;  // tau = 0 pairs a frame with itself: D = 0 exactly
+    // tau = 0 pairs a frame with itself: D = 0 exactly (in a cross pass it pairs two different frames)
+    if (!cross)
+        while (j < nd && delays[j] == 0) ++j;
     while (j < nd) {
         const int j0 = j, d0 = delays[j];
         int len = 1;
@@ -53,7 +55,9 @@ bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, s
     const int K = kDelayBlock, SB = kSlotBuf, SPAN = 64;
     // needed frame range of every consumer step, relative to t0: step 0 reads the block itself
     std::vector<int> need_lo(1, 0), need_hi(1, K - 1);
-    int lo_prev = 0;  // frames t0 + lo_prev .. are in the buffer after the block is loaded
+    // frames t0 + lo_prev .. are in the buffer after the block is loaded (a cross pass's block is
+    // made of other frames than the older sequence it is paired with: none of those are loaded)
+    int lo_prev = cross ? K : 0;
     size_t r = 0;
     while (r < srs->size()) {
         Stage st;
@@ -88,11 +92,12 @@ bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *srs, s
         if (st.lo <= st.hi) {
             for (int q = g - 1; q >= 0; --q) {  // latest earlier step that reads a row the group overwrites
                 // frames f in [lo, hi] and h in [need_lo, need_hi] share a row iff h = f + k SB, k != 0
+                // (k = 0 too against a cross pass's block: the same index there is another frame)
                 bool clash = false;
                 const int a = st.lo, b = st.hi, c = need_lo[q], d = need_hi[q];
                 const int kmin = (int)std::floor((double)(c - b) / SB), kmax = (int)std::ceil((double)(d - a) / SB);
                 for (int k = kmin; k <= kmax && !clash; ++k)
-                    if (k != 0 && std::max(a, c - k * SB) <= std::min(b, d - k * SB)) clash = true;
+                    if ((k != 0 || (cross && q == 0)) && std::max(a, c - k * SB) <= std::min(b, d - k * SB)) clash = true;
                 if (clash) {
                     need = std::max(need, q + 1);
                     break;
@@ -416,7 +421,7 @@ template <bool PACKED>
 __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict__ ring, int R, size_t M,
                                           long long t0, int nb, const DelaySchedule &sched, int nst, int nbatch,
                                           float2 *__restrict__ acc, int nd, int *__restrict__ err, int stall_group,
-                                          size_t tile)
+                                          size_t tile, const float2 *__restrict__ ring_cur = nullptr, int R_cur = 0)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -470,8 +475,9 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                 if (!ok) break;
                 __threadfence_block();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                if (g == 0)
-                    issue_group(S, ring, R, tile, t0, 0, kDelayBlock - 1, &S.full[0]);
+                if (g == 0)  // the block's own frames (in a cross pass: from the other sequence's ring)
+                    issue_group(S, ring_cur ? ring_cur : ring, ring_cur ? R_cur : R, tile, t0, 0, kDelayBlock - 1,
+                                &S.full[0]);
                 else
                     issue_group(S, ring, R, tile, t0, sched.st[g - 1].lo, sched.st[g - 1].hi, &S.full[g % kFullBars]);
                 issued = g + 1;
@@ -574,11 +580,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                                                                  long long t0, int nb,
                                                                  const __grid_constant__ DelaySchedule sched,
                                                                  float2 *__restrict__ acc, int nd,
-                                                                 int *__restrict__ err, int stall_group)
+                                                                 int *__restrict__ err, int stall_group,
+                                                                 const float2 *__restrict__ ring_cur, int R_cur)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
-    tile_pass<PACKED>(S, ring, R, M, t0, nb, sched, sched.nst, sched.nbatch, acc, nd, err, stall_group, blockIdx.x);
+    tile_pass<PACKED>(S, ring, R, M, t0, nb, sched, sched.nst, sched.nbatch, acc, nd, err, stall_group, blockIdx.x,
+                      ring_cur, R_cur);
 }
 
 // Ragged batch: one persistent launch over the tiles of several sequences (each with its own frame
@@ -684,6 +692,7 @@ constexpr int kBlockMax = 32;
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
 {
     if (a.nb <= 0) return cudaSuccess;
+    if (a.ring_cur && (variant == 1 || !a.sched)) return cudaErrorNotSupported;  // cross passes: tiled only
     if (variant == 1 || !a.sched) {
         // simple kernel, in sub-blocks of up to 32 frames (all frames of the block are in the ring)
         for (int o = 0; o < a.nb; o += kBlockMax) {
@@ -713,13 +722,13 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
                                              (int)smem);
         if (e != cudaSuccess) return e;
         k_delay_f32_tiled<false><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
-                                                               a.stall_group);
+                                                               a.stall_group, a.ring_cur, a.R_cur);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         k_delay_f32_tiled<true><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
-                                                              a.stall_group);
+                                                              a.stall_group, a.ring_cur, a.R_cur);
     }
     return cudaGetLastError();
 }

@@ -96,6 +96,12 @@ struct nfs_ctx {
     double *d_D = nullptr, *d_export = nullptr;
     DelaySchedule *sched = nullptr;  // tiled-kernel schedule (host copy, passed by value); NULL if too long
     int *d_err = nullptr;
+    // Cross pass (one band of the out-of-core mode): pairs (block frame of the "current" sequence,
+    // older frame of the "old" sequence); the current sequence's spectra go to d_ring_cur (K slots),
+    // the old sequence's to d_ring.  Both sequences advance together: frame u of each per step.
+    bool cross = false;
+    void *d_ring_cur = nullptr;
+    long long transforms = 0;  // frames transformed (both sequences of a cross pass)
 
     std::vector<long long> counts, pairs_h;
     std::vector<double> qmean;
@@ -289,6 +295,7 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_sums);
     cudaFree(c->d_ref);
     cudaFree(c->d_ring);
+    cudaFree(c->d_ring_cur);
     cudaFree(c->d_acc);
     cudaFree(c->d_delays);
     cudaFree(c->d_tw_row);
@@ -339,6 +346,10 @@ int flush_block(nfs_ctx *c)
     a.err = c->d_err;
     a.tau_max = c->tau_max;
     a.stall_group = c->stall_group;
+    if (c->cross) {
+        a.ring_cur = (const float2 *)c->d_ring_cur;
+        a.R_cur = c->K;
+    }
     int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
                    "delay_f32");
     if (rc) return rc;
@@ -347,7 +358,10 @@ int flush_block(nfs_ctx *c)
 }
 
 // Transform nf device-resident frames (nf <= fft chunk) and, when a block is complete, update.
-int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
+// A cross context takes the old sequence's frames first (old = true: into the ring at the slots of
+// frames nframes .., no count, no update) and then the same number of the current sequence's
+// frames (into the K-slot current ring; these count and trigger the update).
+int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old = false)
 {
     CK(c, cudaMemsetAsync(c->d_sums, 0, sizeof(unsigned long long) * (size_t)nf, c->stream));
     int rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_frame_sums(dsrc, nf, c->g, c->d_sums, c->stream); },
@@ -359,19 +373,24 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf)
         if (rc) return rc;
         c->have_ref = true;
     }
-    const int slot0 = (int)(c->nframes % c->R);
+    c->transforms += nf;
+    const bool to_cur = c->cross && !old;
+    float2 *ring = (float2 *)(to_cur ? c->d_ring_cur : c->d_ring);
+    const int R = to_cur ? c->K : c->R;
+    const int slot0 = (int)(c->nframes % R);
     if (c->f32()) {
         rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
             return launch_row_fft<float>(dsrc, nf, c->d_sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
-                                         (const float2 *)c->d_tw_post, (float2 *)c->d_ring, c->R, slot0, c->stream,
+                                         (const float2 *)c->d_tw_post, ring, R, slot0, c->stream,
                                          c->d_scratch, c->fft_generic ? nullptr : c->d_tws_row);
         }, "row_fft_f32");
         if (rc) return rc;
         rc = timed(c, NFS_STAGE_COLFFT, c->stream, [&] {
-            return launch_col_fft<float>(nf, c->g, c->plan_col, (const float2 *)c->d_tw_col, (float2 *)c->d_ring, c->R,
+            return launch_col_fft<float>(nf, c->g, c->plan_col, (const float2 *)c->d_tw_col, ring, R,
                                          slot0, c->stream, c->d_scratch, c->fft_generic ? nullptr : c->d_tws_col);
         }, "col_fft_f32");
         if (rc) return rc;
+        if (old) return NFS_OK;
         c->nframes += nf;
         if (c->nframes - c->nprocessed >= c->K && !c->defer_delay) return flush_block(c);
         return NFS_OK;
@@ -472,9 +491,11 @@ int enter(nfs_ctx *c)
     return c->err;
 }
 
-int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out)
+int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
+                bool cross = false)
 {
     if (!out) return NFS_EINVAL;
+    if (cross && path != NFS_PATH_FUSED_F32) return NFS_EINVAL;
     *out = nullptr;
     if (!delays || n_delays <= 0 || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
     if (path != NFS_PATH_FUSED_F32 && path != NFS_PATH_PLAIN_F64) return NFS_EINVAL;
@@ -491,6 +512,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     cudaGetDevice(&c->device);
     c->path = path;
     c->K = block ? block : kDefaultBlock;
+    c->cross = cross;
     c->nd = n_delays;
     c->nq = n_qbins;
     c->delays.assign(delays, delays + n_delays);
@@ -534,6 +556,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * kMaxChunk))) return bail(rc);
     if (c->f32() && (rc = alloc_dev(c, (void **)&c->d_ref, sizeof(float) * c->g.HW))) return bail(rc);
     if ((rc = alloc_dev(c, &c->d_ring, ring_bytes))) return bail(rc);
+    if (cross && (rc = alloc_dev(c, &c->d_ring_cur, (size_t)c->K * c->g.M * c->csize()))) return bail(rc);
     if ((rc = alloc_dev(c, &c->d_acc, acc_bytes))) return bail(rc);
     if ((rc = alloc_dev(c, (void **)&c->d_delays, sizeof(int) * (size_t)c->nd))) return bail(rc);
     if ((rc = alloc_dev(c, (void **)&c->d_pairs, sizeof(long long) * (size_t)c->nd))) return bail(rc);
@@ -559,7 +582,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     if (c->f32()) {
         std::vector<SubRun> srs;
         std::vector<Stage> sts;
-        if (!build_delay_schedule(c->delays.data(), c->nd, &srs, &sts)) return bail(NFS_EUNSUPPORTED);
+        if (!build_delay_schedule(c->delays.data(), c->nd, cross, &srs, &sts)) return bail(NFS_EUNSUPPORTED);
         // a delay list too long for the parameter-space schedule uses the one-thread-per-mode kernel
         if (srs.size() <= (size_t)kMaxSubRuns && sts.size() <= (size_t)kMaxSchedStages) {
             c->sched = new (std::nothrow) DelaySchedule();
@@ -570,6 +593,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
             std::copy(srs.begin(), srs.end(), c->sched->sr);
             std::copy(sts.begin(), sts.end(), c->sched->st);
         }
+        if (cross && !c->sched) return bail(NFS_EUNSUPPORTED);  // cross passes run on the tiled kernel only
     }
     *out = c;
     return NFS_OK;
@@ -1096,7 +1120,7 @@ int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const
     for (int s = 0; s < b->n; ++s)
         if (n_frames[s] < 0 || (n_frames[s] > 0 && !dev_frames[s])) return NFS_EINVAL;
     for (;;) {
-        bool left = false, moved = false;
+        bool left = false;
         for (int s = 0; s < b->n; ++s) {
             nfs_ctx *c = b->seq[s];
             const long long rem = n_frames[s] - done[s];
@@ -1107,10 +1131,8 @@ int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const
             const int m = (int)std::min(room, rem);
             if ((rc = nfs_push_frames_device(c, dev_frames[s] + (size_t)done[s] * c->g.HW, m))) return rc;
             done[s] += m;
-            moved = true;
         }
         if (!left) break;
-        (void)moved;
         // every member that still has frames now holds a full block: one launch for all of them
         if ((rc = batch_flush(b, false))) return rc;
     }
@@ -1157,5 +1179,198 @@ int64_t nfs_batch_launch_count(const nfs_batch *b)
 }
 
 const char *nfs_batch_last_error(const nfs_batch *b) { return b ? b->errmsg.c_str() : ""; }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ out-of-core bands
+//
+// When the ring for every delay does not fit, the delays are split into bands processed one after
+// the other, each re-reading the frames from host memory (the paper's FIFO re-upload, organised
+// by delay bands).  Band 0 is an ordinary pass over the delays d with d + K <= the slot budget.
+// A later band with smallest delay lo takes the shift s = floor(lo / K) K and runs a cross pass:
+// current sequence C_u = frame u + s (K-slot ring), old sequence O_u = frame u (ring of
+// e_max + K slots), delays e = d - s, so the pair (C_u, O_{u-e}) is the pair (u + s, u + s - d).
+// The block boundaries of C fall on multiples of K in the original frame index (s is a multiple
+// of K), so every pair is added in the same block and warp as in one in-core pass.
+
+namespace {
+
+// One band: delays [first, last) of the list, shift s (s = 0: the ordinary pass).
+struct Band {
+    int first, last;
+    long long shift;
+};
+
+// Does the tiled kernel's schedule of these (shifted) delays fit its parameter space?
+bool schedule_fits(const std::vector<int> &d, bool cross)
+{
+    std::vector<SubRun> srs;
+    std::vector<Stage> sts;
+    if (!build_delay_schedule(d.data(), (int)d.size(), cross, &srs, &sts)) return false;
+    return srs.size() <= (size_t)kMaxSubRuns && sts.size() <= (size_t)kMaxSchedStages;
+}
+
+int plan_bands(const int32_t *delays, int nd, long long N, long long max_slots, std::vector<Band> *bands,
+               long long *n_transforms)
+{
+    bands->clear();
+    *n_transforms = 0;
+    const long long K = kDefaultBlock;
+    int j = 0;
+    while (j < nd) {
+        const long long lo = delays[j];
+        const bool first = bands->empty();
+        // band 0 runs in place when its first delay fits; later bands are cross passes
+        const bool in_place = first && lo + K <= max_slots;
+        const long long s = in_place ? 0 : lo / K * K;
+        const long long hi_max = in_place ? max_slots - K : max_slots - 2 * K + s;
+        // a cross pass needs its first delay within the budget (always so for budgets of 3K slots)
+        if (!in_place && (lo < K || lo > hi_max)) return NFS_EINVAL;
+        int e = j;
+        while (e < nd && delays[e] <= hi_max) ++e;
+        // keep the band within the tiled kernel's schedule limits
+        for (;;) {
+            std::vector<int> d;
+            for (int q = j; q < e; ++q) d.push_back((int)(delays[q] - s));
+            if (schedule_fits(d, !in_place)) break;
+            e = j + (e - j) / 2;
+            if (e == j) return NFS_EUNSUPPORTED;
+        }
+        bands->push_back({j, e, s});
+        if (in_place)
+            *n_transforms += N;
+        else if (N > s)
+            *n_transforms += 2 * (N - s);
+        j = e;
+    }
+    return NFS_OK;
+}
+
+// A cross pass over host frames: old sequence `old` and current sequence `cur`, n frames each
+// (pinned or pageable; read before the call returns).
+int cross_push(nfs_ctx *c, const uint16_t *cur, const uint16_t *old, long long n)
+{
+    const bool locked = is_page_locked(cur) && is_page_locked(old);
+    if (!locked && !c->h_stage[0]) {
+        for (int i = 0; i < 2; ++i) {
+            cudaError_t e = cudaMallocHost((void **)&c->h_stage[i], c->frame_bytes() * (size_t)c->copy_frames);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return NFS_ENOMEM;
+            }
+        }
+    }
+    // copy nc frames from src into the next staging slot; returns the slot
+    auto stage = [&](const uint16_t *src, int nc, int *slot_out) -> int {
+        const int slot = (int)(c->stage_i++ % c->n_slots);
+        uint16_t *dst = c->d_stage + (size_t)slot * c->copy_frames * c->g.HW;
+        const size_t bytes = c->frame_bytes() * (size_t)nc;
+        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[slot], 0));
+        int hs = -1;
+        if (!locked) {
+            hs = (int)(c->hstage_i++ & 1);
+            CK(c, cudaEventSynchronize(c->ev_hcopied[hs]));
+            memcpy(c->h_stage[hs], src, bytes);
+            src = c->h_stage[hs];
+        }
+        const int rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
+            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
+        }, "h2d");
+        if (rc) return rc;
+        if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
+        CK(c, cudaEventRecord(c->ev_filled[slot], c->copy_stream));
+        CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[slot], 0));
+        *slot_out = slot;
+        return NFS_OK;
+    };
+    long long done = 0;
+    int last = -1;
+    while (done < n) {
+        const int nc = (int)std::min<long long>(c->copy_frames, n - done);
+        int so = 0, sc = 0, rc;
+        if ((rc = stage(old + (size_t)done * c->g.HW, nc, &so))) return rc;
+        if ((rc = stage(cur + (size_t)done * c->g.HW, nc, &sc))) return rc;
+        const uint16_t *dold = c->d_stage + (size_t)so * c->copy_frames * c->g.HW;
+        const uint16_t *dcur = c->d_stage + (size_t)sc * c->copy_frames * c->g.HW;
+        for (int o = 0; o < nc;) {
+            const int nf = next_chunk(c, nc - o, c->fft_chunk);
+            if ((rc = process_chunk(c, dold + (size_t)o * c->g.HW, nf, true))) return rc;
+            if ((rc = process_chunk(c, dcur + (size_t)o * c->g.HW, nf, false))) return rc;
+            o += nf;
+        }
+        CK(c, cudaEventRecord(c->ev_free[so], c->stream));
+        CK(c, cudaEventRecord(c->ev_free[sc], c->stream));
+        done += nc;
+        last = sc;
+    }
+    if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_filled[last]));
+    return c->err;
+}
+
+}  // namespace
+
+extern "C" {
+
+int nfs_out_of_core_plan(const int32_t *delays, int n_delays, int64_t n_frames, int64_t max_ring_slots,
+                         int32_t *band_first, int64_t *band_shift, int *n_bands, int64_t *n_transforms)
+{
+    if (!delays || n_delays <= 0 || n_frames < 0 || !n_bands || !n_transforms) return NFS_EINVAL;
+    for (int j = 0; j < n_delays; ++j)
+        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
+    std::vector<Band> bands;
+    long long nt = 0;
+    const int rc = plan_bands(delays, n_delays, n_frames, max_ring_slots, &bands, &nt);
+    if (rc) return rc;
+    *n_bands = (int)bands.size();
+    *n_transforms = nt;
+    for (size_t b = 0; b < bands.size(); ++b) {
+        if (band_first) band_first[b] = bands[b].first;
+        if (band_shift) band_shift[b] = bands[b].shift;
+    }
+    if (band_first) band_first[bands.size()] = n_delays;
+    return NFS_OK;
+}
+
+int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int n_delays, int n_qbins,
+                                       const uint16_t *frames, int64_t n_frames, int64_t max_ring_slots, double *D,
+                                       int64_t *bin_counts, int64_t *pair_counts, double *q_mean,
+                                       int64_t *n_transforms)
+{
+    if (!delays || n_delays <= 0 || n_qbins <= 0 || !D || !bin_counts || !pair_counts) return NFS_EINVAL;
+    if (n_frames < 0 || n_frames > 0x7fffffffLL || (n_frames > 0 && !frames)) return NFS_EINVAL;
+    for (int j = 0; j < n_delays; ++j)
+        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
+    std::vector<Band> bands;
+    long long planned = 0;
+    int rc = plan_bands(delays, n_delays, n_frames, max_ring_slots, &bands, &planned);
+    if (rc) return rc;
+    const size_t HW = (size_t)H * W;
+    long long done = 0;
+    std::vector<double> Db;
+    std::vector<int64_t> pc;
+    for (const Band &b : bands) {
+        const int nb = b.last - b.first;
+        std::vector<int32_t> d(delays + b.first, delays + b.last);
+        for (int32_t &x : d) x -= (int32_t)b.shift;
+        nfs_ctx *c = nullptr;
+        rc = create_impl(H, W, d.data(), nb, n_qbins, NFS_PATH_FUSED_F32, 0, &c, b.shift > 0);
+        if (rc) return rc;
+        Db.assign((size_t)nb * n_qbins, 0.0);
+        pc.assign((size_t)nb, 0);
+        if (b.shift == 0)
+            rc = n_frames > 0 ? nfs_push_frames(c, frames, (int)n_frames) : NFS_OK;
+        else if (n_frames > b.shift)
+            rc = cross_push(c, frames + (size_t)b.shift * HW, frames, n_frames - b.shift);
+        if (!rc) rc = nfs_structure_function(c, Db.data(), bin_counts, pc.data(), q_mean);
+        done += c->transforms;
+        nfs_destroy(c);
+        if (rc) return rc;
+        std::copy(Db.begin(), Db.end(), D + (size_t)b.first * n_qbins);
+        for (int q = 0; q < nb; ++q) pair_counts[b.first + q] = n_frames > b.shift ? pc[q] : 0;
+    }
+    if (done != planned) return NFS_ESTATE;  // the passes transformed other frames than planned
+    if (n_transforms) *n_transforms = done;
+    return NFS_OK;
+}
 
 }  // extern "C"

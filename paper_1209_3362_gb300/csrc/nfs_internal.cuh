@@ -125,7 +125,10 @@ constexpr int kFullBars = 4;       // copy-group mbarriers of the tiled kernel (
 constexpr int kDelayErrWords = 48; // status words of the tiled kernel
 constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
 constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
-bool build_delay_schedule(const int *delays, int nd, std::vector<SubRun> *subruns, std::vector<Stage> *stages);
+// cross: a cross pass (the block's frames belong to one sequence, the older frames of every pair
+// to another, indexed alike; delay 0 is a real pair), see DelayArgs::ring_cur
+bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *subruns,
+                          std::vector<Stage> *stages);
 int count_delay_batches(const std::vector<SubRun> &subruns);  // batches the consumers hand to the writer
 
 // The schedule travels by value in the kernel parameters (constant bank): uniform, cached reads.
@@ -152,6 +155,11 @@ struct DelayArgs {
     int *err;     // device status words (kDelayErrWords): [0] set when a bounded wait gives up, [1..] where
     int tau_max;
     int stall_group;  // test hook: the producer stops before this copy group (-1: off)
+    // Cross pass (out-of-core bands): the block's new frames t0 .. t0+nb-1 come from ring_cur
+    // (R_cur slots, frame t in slot t mod R_cur) and every older frame of a pair from ring; a pair
+    // at delay d is (block frame t, ring frame t - d), d = 0 included.  NULL: one ring for both.
+    const float2 *ring_cur = nullptr;
+    int R_cur = 0;
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
 

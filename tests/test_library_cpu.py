@@ -69,3 +69,56 @@ def test_no_cpu_fallback_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(root, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text and "nfsor_" not in text, f
+
+
+# ---------------------------------------------------------------- out-of-core band plan (host logic)
+
+K = 256
+
+
+def _check_plan(delays, N, Rmax):
+    p = P.out_of_core_plan(delays, N, Rmax)
+    first, shift = list(p["band_first"]), list(p["band_shift"])
+    assert first[0] == 0 and first[-1] == len(delays) and len(first) == len(shift) + 1
+    assert all(a < b for a, b in zip(first, first[1:]))  # every delay in exactly one band, in order
+    expect = 0
+    for b, s in enumerate(shift):
+        d = delays[first[b]:first[b + 1]]
+        if s == 0:
+            assert b == 0 and d[-1] + K <= Rmax  # in place: ring of d_max + K slots
+            expect += N
+        else:
+            assert s % K == 0 and s == d[0] // K * K  # shifted pass: blocks stay on multiples of K
+            assert (d[-1] - s) + 2 * K <= Rmax  # old-frame ring plus the K-slot current ring
+            expect += 2 * max(0, N - s)
+    assert p["n_transforms"] == expect
+    return p
+
+
+@pytest.mark.parametrize("Rmax", [3000, 2256, 1500, 1000, 768])
+def test_out_of_core_plan_log_delays(lib, Rmax):
+    d = [int(x) for x in __import__("nfs_synth").log_delays(1, 2000, 200)]
+    p = _check_plan(d, 4000, Rmax)
+    if Rmax >= 2000 + K:
+        assert len(p["band_shift"]) == 1 and p["n_transforms"] == 4000  # fits: one ordinary pass
+
+
+def test_out_of_core_plan_all_delays_against_the_paper_count(lib):
+    """All N - 1 delays (the paper's own case) with memory for N* spectra: our band passes against
+    the paper's FIFO count N (2 alpha - 3 + 2/alpha), alpha = (N - 1) / N*.  With budgets well above
+    the 2K slots a shifted pass spends on its blocks the bands transform fewer frames than the
+    paper's scheme; near 2K they transform more (each band then covers few delays)."""
+    for N, Ns, lower in ((8193, 2048, True), (16385, 4096, True), (4097, 768, False)):
+        p = _check_plan(list(range(1, N)), N, Ns)
+        a = (N - 1) / Ns
+        paper = N * (2 * a - 3 + 2 / a)
+        assert (p["n_transforms"] < paper) == lower, (N, Ns, p["n_transforms"], paper)
+
+
+def test_out_of_core_plan_rejects(lib):
+    with pytest.raises(P.NFSError):
+        P.out_of_core_plan([1, 2, 3070], 4000, 700)  # 3070 - 2816 + 2K > 700: the band cannot hold it
+    with pytest.raises(P.NFSError):
+        P.out_of_core_plan([5, 3], 100, 4000)  # not increasing
+    p = P.out_of_core_plan([0, 1, 2], 10, 300)  # tau = 0 stays in the ordinary band
+    assert list(p["band_first"]) == [0, 3] and p["n_transforms"] == 10
