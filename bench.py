@@ -55,8 +55,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "721b0d5cbd970bd4cba4d4a356c37f6a592b01bfe38b761c49d186074442bec9",
-                         "dram_bytes_per_alg_byte": 0.9949}
+NCU_DELAY_CALIBRATION = {"sha256": "7acba010a6febc1ac223fbcd4599541b5bdc4e389d7bcf0f4fba6f8de61c4e47",
+                         "dram_bytes_per_alg_byte": 0.9955}
 
 
 def delay_kernel_sha():
@@ -281,7 +281,9 @@ def main():
 
     for _ in range(max(args.warmup, 0)):
         step()
-    ctx.set_option(P.OPT_TIMING, 1)
+    # events around the delay-update launches only (the roofline's kernel); events around all
+    # ~3000 launches of a pass would cost several per cent of the step
+    ctx.set_option(P.OPT_TIMING, 2)
     ctx.reset_timings()
     l0 = ctx.launch_count
     barrier()
@@ -328,7 +330,12 @@ def main():
                 "launch_ms": per_launch_ms, "launches": n_launch,
                 "hbm": {"achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s", "frac": hbm_achieved / hbm_peak,
                         "peak_source": f"{peak_src} hbm_gbs"}}
-    stage_ms = {k: v[0] / args.steps for k, v in tim.items()}
+    # per-stage breakdown: one more pass with events around every launch (not part of the timed region)
+    ctx.set_option(P.OPT_TIMING, 1)
+    ctx.reset_timings()
+    step()
+    stage_ms = {k: v[0] for k, v in ctx.timings().items()}
+    ctx.set_option(P.OPT_TIMING, 0)
 
     # ---- end to end from pinned host memory
     e2e = None

@@ -135,7 +135,8 @@ const char *nfs_last_error(const nfs_ctx *ctx);
 void *nfs_get_stream(const nfs_ctx *ctx);
 
 /* Option keys for nfs_set_option / nfs_get_option. */
-#define NFS_OPT_TIMING 1      /* 1 = record CUDA events around every kernel launch (default 0) */
+#define NFS_OPT_TIMING 1      /* 1 = record CUDA events around every kernel launch; 2 = around the
+                                  delay-update launches only (the least overhead); default 0 */
 #define NFS_OPT_BLOCK_FRAMES 2 /* read-only: K */
 #define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K (FP32) or tau_max + 64 (FP64) */
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */

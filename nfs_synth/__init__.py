@@ -104,6 +104,9 @@ WORKLOADS = {
     # 4000 frames of 2048x2048, 200 log delays 1..2000, 1024 bins, Gamma = q^2 + 0.01.
     "ddm2048": Workload("ddm2048", 4000, 2048, 2048, tuple(log_delays(1, 2000, 200)), 1024, 1.0, 0.01, 0.05,
                         12093365),
+    # The paper's largest-speed-up case: 2048 frames of 512x512 and every delay 1..2047 (all N - 1
+    # delays, as the paper's program computes them), 256 bins, D = 1 px^2/frame.
+    "paper512": Workload("paper512", 2048, 512, 512, tuple(range(1, 2048)), 256, 1.0, 0.0, 0.05, 12093368),
 }
 
 

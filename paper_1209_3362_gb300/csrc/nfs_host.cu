@@ -111,7 +111,7 @@ struct nfs_ctx {
     int err = NFS_OK;
     std::string errmsg;
 
-    bool timing = false;
+    int timing = 0;  // 1: events around every launch; 2: around delay-update launches only
     std::vector<TimedPair> pending;
     std::vector<cudaEvent_t> pool;
     double stage_ms[NFS_N_STAGES] = {};
@@ -159,7 +159,8 @@ template <class F>
 int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (c->timing) {
+    const bool on = c->timing == 1 || (c->timing == 2 && stage == NFS_STAGE_DELAY);
+    if (on) {
         a = pool_get(c);
         b = pool_get(c);
         if (!a || !b) return set_cuda_error(c, cudaErrorMemoryAllocation, "cudaEventCreate");
@@ -167,7 +168,7 @@ int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
     }
     cudaError_t e = f();
     if (e != cudaSuccess) return set_cuda_error(c, e, what);
-    if (c->timing) {
+    if (on) {
         CK(c, cudaEventRecord(b, s));
         c->pending.push_back({stage, a, b});
     }
@@ -811,7 +812,10 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
     int rc = enter(c);
     if (rc) return rc;
     switch (key) {
-        case NFS_OPT_TIMING: c->timing = v != 0; return NFS_OK;
+        case NFS_OPT_TIMING:
+            if (v < 0 || v > 2) return NFS_EINVAL;
+            c->timing = (int)v;
+            return NFS_OK;
         case NFS_OPT_FFT_CHUNK:
             if (v == 0 && c->f32()) return autotune_fft_chunk(c);
             if (v < 1 || v > (c->f32() ? kMaxChunkF32 : kMaxChunk)) return NFS_EINVAL;

@@ -300,3 +300,16 @@ def test_out_of_core_bands_match_in_core(oracle_lib, Rmax):
     ref = oracle_lib.structure_function(fr, delays, 32)
     check_counts(got, ref)
     assert rel_err(got, ref) <= TOL_F32
+
+
+def test_all_delays_mode(oracle_lib):
+    """Every delay 1..N-1 (the paper's own analysis): 128 sub-runs of 16 consecutive delays in the
+    tiled kernel's schedule, pairs down to a single one at the largest delay."""
+    N = 300
+    fr = S.OUFrameSource(64, 64, 1.0, seed=55).frames_numpy(N)
+    delays = list(range(1, N))
+    ref = oracle_lib.structure_function(fr, delays, 32)
+    got = run_lib(fr, delays, 32)
+    check_counts(got, ref)
+    assert got["pair_counts"][-1] == 1
+    assert rel_err(got, ref) <= TOL_F32
