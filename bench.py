@@ -163,6 +163,21 @@ def oracle_sample(frames_host, budget_s, cores):
     return n, n * (n - 1) // 2, dt
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over all ranks (every rank gets it); x itself on one process."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, frames_per_rank: int, step_ms: float) -> float:
+    """Whole-job frames/s: the frames all ranks processed over the slowest rank's step time."""
+    return world * frames_per_rank / (step_ms / 1000.0)
+
+
 def run_reference(args, w):
     """The FP64 CPU oracle alone, each step a bounded sample; rank 0 prints."""
     rank = int(os.environ.get("RANK", "0"))
@@ -243,12 +258,8 @@ def main():
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x: float) -> float:
+        return max_over_ranks(x, dist, "cuda")
 
     P.build()
     P.load_library()
@@ -302,8 +313,8 @@ def main():
     barrier()
     launches = ctx.launch_count - l0
     dev_ms = ev0.elapsed_time(ev1)
-    step_ms = max_over_ranks(max(dev_ms, 1000.0 * wall) / args.steps)
-    value = world * w.N / (step_ms / 1000.0)
+    step_ms = ranks_max(max(dev_ms, 1000.0 * wall) / args.steps)
+    value = job_value(world, w.N, step_ms)
     tim = ctx.timings()
     D32 = res["D"]
 
@@ -357,8 +368,8 @@ def main():
         t0 = time.perf_counter()
         for _ in range(args.steps):
             step_host()
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
-        e2e = {"value": world * w.N / e2e_s, "unit": "frames/s", "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
+        e2e_s = ranks_max((time.perf_counter() - t0) / args.steps)
+        e2e = {"value": job_value(world, w.N, 1000.0 * e2e_s), "unit": "frames/s", "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
                "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
     ctx.close()
 
@@ -377,10 +388,10 @@ def main():
         r64 = c64.structure_function()
         e1.record(s64)
         e1.synchronize()
-        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        ms64 = ranks_max(e0.elapsed_time(e1))
         m = (r64["bin_counts"][None, :] > 0) & (r64["pair_counts"][:, None] > 0)
         err = float(np.max(np.abs(D32[m] - r64["D"][m]) / np.abs(r64["D"][m])))
-        plain = {"value": world * w.N / (ms64 / 1000.0), "unit": "frames/s", "ms_per_pass": ms64,
+        plain = {"value": job_value(world, w.N, ms64), "unit": "frames/s", "ms_per_pass": ms64,
                  "max_rel_err_f32_vs_f64": err}
         c64.close()
 
