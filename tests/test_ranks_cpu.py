@@ -31,7 +31,7 @@ def test_two_rank_aggregation():
     world, frames = 2, 4000
     times = [531.0, 560.5]  # per-rank ms per step
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank, args=(world, port, times, frames, out), nprocs=world, join=True)
         res = dict(out)
