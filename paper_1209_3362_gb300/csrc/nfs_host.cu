@@ -358,22 +358,31 @@ int flush_block(nfs_ctx *c)
     return NFS_OK;
 }
 
-// Transform nf device-resident frames (nf <= fft chunk) and, when a block is complete, update.
-// A cross context takes the old sequence's frames first (old = true: into the ring at the slots of
-// frames nframes .., no count, no update) and then the same number of the current sequence's
-// frames (into the K-slot current ring; these count and trigger the update).
-int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old = false)
+// Exact spatial sums of n device-resident frames (n <= kMaxChunk) into sums[0 .. n), in one launch
+// for a whole copy chunk; the reference image comes from the first frame the context ever sees.
+int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums)
 {
-    CK(c, cudaMemsetAsync(c->d_sums, 0, sizeof(unsigned long long) * (size_t)nf, c->stream));
-    int rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_frame_sums(dsrc, nf, c->g, c->d_sums, c->stream); },
+    CK(c, cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * (size_t)n, c->stream));
+    int rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_frame_sums(dsrc, n, c->g, sums, c->stream); },
                    "frame_sums");
     if (rc) return rc;
     if (!c->have_ref && c->f32()) {
-        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, c->d_sums, c->g, c->d_ref, c->stream); },
+        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, sums, c->g, c->d_ref, c->stream); },
                    "reference");
         if (rc) return rc;
         c->have_ref = true;
     }
+    return NFS_OK;
+}
+
+// Transform nf device-resident frames (nf <= fft chunk) whose sums are in sums[0 .. nf) and, when a
+// block is complete, update.  A cross context takes the old sequence's frames first (old = true:
+// into the ring at the slots of frames nframes .., no count, no update) and then the same number
+// of the current sequence's frames (into the K-slot current ring; these count and trigger the
+// update).
+int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old, const unsigned long long *sums)
+{
+    int rc = NFS_OK;
     c->transforms += nf;
     const bool to_cur = c->cross && !old;
     float2 *ring = (float2 *)(to_cur ? c->d_ring_cur : c->d_ring);
@@ -381,7 +390,7 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old = false)
     const int slot0 = (int)(c->nframes % R);
     if (c->f32()) {
         rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
-            return launch_row_fft<float>(dsrc, nf, c->d_sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
+            return launch_row_fft<float>(dsrc, nf, sums, c->d_ref, c->g, c->plan_row, (const float2 *)c->d_tw_row,
                                          (const float2 *)c->d_tw_post, ring, R, slot0, c->stream,
                                          c->d_scratch, c->fft_generic ? nullptr : c->d_tws_row);
         }, "row_fft_f32");
@@ -397,7 +406,7 @@ int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old = false)
         return NFS_OK;
     }
     rc = timed(c, NFS_STAGE_ROWFFT, c->stream, [&] {
-        return launch_row_fft<double>(dsrc, nf, c->d_sums, nullptr, c->g, c->plan_row, (const double2 *)c->d_tw_row,
+        return launch_row_fft<double>(dsrc, nf, sums, nullptr, c->g, c->plan_row, (const double2 *)c->d_tw_row,
                                       (const double2 *)c->d_tw_post, (double2 *)c->d_ring, c->R, slot0, c->stream);
     }, "row_fft_f64");
     if (rc) return rc;
@@ -554,7 +563,8 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
         return bail(rc);
     const size_t ring_bytes = (size_t)c->R * c->g.M * c->csize();
     const size_t acc_bytes = (size_t)c->nd * c->g.M * c->asize();
-    if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * kMaxChunk))) return bail(rc);
+    // sums of up to two copy chunks (a cross pass stages one of each sequence)
+    if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * 2 * kMaxChunk))) return bail(rc);
     if (c->f32() && (rc = alloc_dev(c, (void **)&c->d_ref, sizeof(float) * c->g.HW))) return bail(rc);
     if ((rc = alloc_dev(c, &c->d_ring, ring_bytes))) return bail(rc);
     if (cross && (rc = alloc_dev(c, &c->d_ring_cur, (size_t)c->K * c->g.M * c->csize()))) return bail(rc);
@@ -666,9 +676,10 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
         if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
         CK(c, cudaEventRecord(c->ev_filled[slot], c->copy_stream));
         CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[slot], 0));
+        if ((rc = frame_sums(c, dst, nc, c->d_sums))) return rc;
         for (int o = 0; o < nc;) {
             const int nf = next_chunk(c, nc - o, c->fft_chunk);
-            rc = process_chunk(c, dst + (size_t)o * c->g.HW, nf);
+            rc = process_chunk(c, dst + (size_t)o * c->g.HW, nf, false, c->d_sums + o);
             if (rc) return rc;
             o += nf;
         }
@@ -688,10 +699,15 @@ int nfs_push_frames_device(nfs_ctx *c, const uint16_t *d, int n)
     if (n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 1)) return NFS_EINVAL;
     long long done = 0;
     while (done < n) {
-        const int nf = next_chunk(c, n - done, c->fft_chunk);
-        rc = process_chunk(c, d + (size_t)done * c->g.HW, nf);
-        if (rc) return rc;
-        done += nf;
+        const int ng = (int)std::min<long long>(kMaxChunk, n - done);
+        const uint16_t *grp = d + (size_t)done * c->g.HW;
+        if ((rc = frame_sums(c, grp, ng, c->d_sums))) return rc;
+        for (int o = 0; o < ng;) {
+            const int nf = next_chunk(c, ng - o, c->fft_chunk);
+            if ((rc = process_chunk(c, grp + (size_t)o * c->g.HW, nf, false, c->d_sums + o))) return rc;
+            o += nf;
+        }
+        done += ng;
     }
     return c->err;
 }
@@ -1296,10 +1312,13 @@ int cross_push(nfs_ctx *c, const uint16_t *cur, const uint16_t *old, long long n
         if ((rc = stage(cur + (size_t)done * c->g.HW, nc, &sc))) return rc;
         const uint16_t *dold = c->d_stage + (size_t)so * c->copy_frames * c->g.HW;
         const uint16_t *dcur = c->d_stage + (size_t)sc * c->copy_frames * c->g.HW;
+        // the old sequence's first frame (frame 0) gives the reference image
+        if ((rc = frame_sums(c, dold, nc, c->d_sums))) return rc;
+        if ((rc = frame_sums(c, dcur, nc, c->d_sums + kMaxChunk))) return rc;
         for (int o = 0; o < nc;) {
             const int nf = next_chunk(c, nc - o, c->fft_chunk);
-            if ((rc = process_chunk(c, dold + (size_t)o * c->g.HW, nf, true))) return rc;
-            if ((rc = process_chunk(c, dcur + (size_t)o * c->g.HW, nf, false))) return rc;
+            if ((rc = process_chunk(c, dold + (size_t)o * c->g.HW, nf, true, c->d_sums + o))) return rc;
+            if ((rc = process_chunk(c, dcur + (size_t)o * c->g.HW, nf, false, c->d_sums + kMaxChunk + o))) return rc;
             o += nf;
         }
         CK(c, cudaEventRecord(c->ev_free[so], c->stream));
