@@ -55,8 +55,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "7acba010a6febc1ac223fbcd4599541b5bdc4e389d7bcf0f4fba6f8de61c4e47",
-                         "dram_bytes_per_alg_byte": 0.9955}
+NCU_DELAY_CALIBRATION = {"sha256": "f10b8902b4be3ed440778485a973d545fa17a79e3f6341622b0b490a348ce9a8",
+                         "dram_bytes_per_alg_byte": 0.9951}
 
 
 def delay_kernel_sha():
@@ -277,6 +277,12 @@ def main():
         frames[o:o + n] = src.next_frames(n)
     del src
     torch.cuda.synchronize()
+    # the pinned host copy for the end-to-end run, allocated and filled before the library's own
+    # allocations (as an acquisition program would hold its frame buffer)
+    host = None
+    if not args.no_e2e:
+        host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
+        host.copy_(frames)
 
     ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
     if args.delay_variant:
@@ -351,8 +357,6 @@ def main():
     # ---- end to end from pinned host memory
     e2e = None
     if not args.no_e2e:
-        host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
-        host.copy_(frames)
         del frames
         torch.cuda.empty_cache()
         frames = None
