@@ -278,6 +278,30 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
                                        int64_t *n_transforms);
 
 /*
+ * ---------------------------------------------------------------- delay-kernel schedule (host logic)
+ * nfs_delay_schedule() returns the copy schedule the fused delay kernel follows for a delay list,
+ * so that its safety can be checked without a GPU.  The kernel takes a block of block_frames new
+ * frames t0 .. per launch and streams older frames through a ring of slot_rows shared-memory rows
+ * (frame f in row f mod slot_rows) in copy groups: group 0 brings the block itself, group s + 1 the
+ * frames of stage s not yet present.  Step 0 reads the block; step s + 1 reads stage s's frames.
+ *   delays, n_delays   as for nfs_create (strictly increasing, >= 0)
+ *   cross        nonzero: the schedule of a shifted out-of-core pass (the block's frames and the
+ *                older frames are two different sequences indexed alike; delay 0 is a real pair)
+ *   subruns      [3 * max_entries] or NULL: per sub-run (j0, len, d0): delays j0 .. j0+len-1 are
+ *                d0 .. d0+len-1 (runs of consecutive delays, at most 16)
+ *   stages       [5 * max_entries] or NULL: per stage (first sub-run, sub-runs, lo, hi, need): its
+ *                copy group loads frames t0+lo .. t0+hi (none when lo > hi) and may be issued once
+ *                steps 0 .. need-1 are finished by every warp; the stage reads frames
+ *                t0 - (largest delay) .. t0 + block_frames - 1 - (smallest delay)
+ *   n_subruns, n_stages, block_frames, slot_rows, copy_barriers   out (copy group g waits on
+ *                barrier g mod copy_barriers; the last three may be NULL)
+ * NFS_ETOOBIG if an array would need more than max_entries entries (the counts are still set).
+ */
+int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *subruns, int32_t *stages,
+                       int max_entries, int *n_subruns, int *n_stages, int *block_frames, int *slot_rows,
+                       int *copy_barriers);
+
+/*
  * ---------------------------------------------------------------- analysis without allocation
  * The paper has no counterpart to this entry point; it exists for callers that cannot allocate
  * device memory while they run: a process whose device memory is owned by another allocator

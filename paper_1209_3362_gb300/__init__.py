@@ -88,6 +88,8 @@ def load_library(path: Optional[str] = None):
         "nfs_launch_count": (I64, [V]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
         "nfs_out_of_core_plan": (I, [V, I, I64, I64, V, V, ctypes.POINTER(I), ctypes.POINTER(I64)]),
+        "nfs_delay_schedule": (I, [V, I, I, V, V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
+                                   ctypes.POINTER(I), ctypes.POINTER(I)]),
         "nfs_structure_function_out_of_core": (I, [I, I, V, I, I, V, I64, I64, V, V, V, V, ctypes.POINTER(I64)]),
         "nfs_fit": (I, [V, V, V, V, V, I, I]),
         "nfs_batch_create": (I, [I, V, V, V, V, V, PP]),
@@ -299,6 +301,22 @@ def out_of_core_plan(delays, n_frames: int, max_ring_slots: int) -> dict:
         raise NFSError(rc, "nfs_out_of_core_plan")
     n = nb.value
     return dict(band_first=first[:n + 1].copy(), band_shift=shift[:n].copy(), n_transforms=nt.value)
+
+
+def delay_schedule(delays, cross: bool = False) -> dict:
+    """The fused delay kernel's copy schedule for a delay list (host logic; see nfs_delay_schedule)."""
+    L = load_library()
+    d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
+    cap = max(16, d.size)
+    sr = np.zeros((cap, 3), np.int32)
+    st = np.zeros((cap, 5), np.int32)
+    out = [ctypes.c_int(0) for _ in range(5)]
+    rc = L.nfs_delay_schedule(_ptr(d), int(d.size), int(bool(cross)), _ptr(sr), _ptr(st), cap,
+                              *[ctypes.byref(o) for o in out])
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_delay_schedule")
+    nsr, nst, K, rows, bars = (o.value for o in out)
+    return dict(subruns=sr[:nsr].copy(), stages=st[:nst].copy(), block_frames=K, slot_rows=rows, copy_barriers=bars)
 
 
 def structure_function_out_of_core(frames, delays, n_qbins: int, max_ring_slots: int) -> dict:

@@ -1397,3 +1397,34 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
 }
 
 }  // extern "C"
+
+extern "C" int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *subruns, int32_t *stages,
+                                  int max_entries, int *n_subruns, int *n_stages, int *block_frames,
+                                  int *slot_rows, int *copy_barriers)
+{
+    if (!delays || n_delays <= 0 || !n_subruns || !n_stages) return NFS_EINVAL;
+    for (int j = 0; j < n_delays; ++j)
+        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
+    std::vector<SubRun> srs;
+    std::vector<Stage> sts;
+    if (!build_delay_schedule(delays, n_delays, cross != 0, &srs, &sts)) return NFS_EUNSUPPORTED;
+    *n_subruns = (int)srs.size();
+    *n_stages = (int)sts.size();
+    if (block_frames) *block_frames = kDelayBlock;
+    if (slot_rows) *slot_rows = kSlotBuf;
+    if (copy_barriers) *copy_barriers = kFullBars;
+    if ((subruns && (int)srs.size() > max_entries) || (stages && (int)sts.size() > max_entries)) return NFS_ETOOBIG;
+    for (size_t i = 0; subruns && i < srs.size(); ++i) {
+        subruns[3 * i] = srs[i].j0;
+        subruns[3 * i + 1] = srs[i].len;
+        subruns[3 * i + 2] = srs[i].d0;
+    }
+    for (size_t i = 0; stages && i < sts.size(); ++i) {
+        stages[5 * i] = sts[i].sr0;
+        stages[5 * i + 1] = sts[i].nsr;
+        stages[5 * i + 2] = sts[i].lo;
+        stages[5 * i + 3] = sts[i].hi;
+        stages[5 * i + 4] = sts[i].need;
+    }
+    return NFS_OK;
+}
