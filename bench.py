@@ -55,8 +55,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "f10b8902b4be3ed440778485a973d545fa17a79e3f6341622b0b490a348ce9a8",
-                         "dram_bytes_per_alg_byte": 0.9951}
+NCU_DELAY_CALIBRATION = {"sha256": "4424f195d80ef0a94dd8302d55453008a46d040c8dd8ba67c9ef6892c1477929",
+                         "dram_bytes_per_alg_byte": 0.9963}
 
 
 def delay_kernel_sha():
@@ -288,7 +288,7 @@ def main():
     if args.delay_variant:
         ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
-    M = (w.H * (w.W // 2 + 1) + 31) // 32 * 32  # modes per spectrum (column-major, padded to 32)
+    M = (w.H * (w.W // 2 + 1) + 15) // 16 * 16  # modes per spectrum (column-major, padded to 16-mode tiles)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def step():

@@ -8,16 +8,18 @@
 // differences" of the processing paragraph).  Averaging over t at fixed tau is the time average
 // that stands for the ensemble average of Eq. 1 for stationary dynamics.
 //
-// Tiled kernel (variant 0).  One CTA owns a tile of 32 consecutive modes for a block of K = 256
-// new frames; 16 warps each take 16 consecutive frames (lane = mode), holding those 16 spectra in
-// registers.  Delays are taken in order as runs of consecutive values ("sub-runs" of up to 16):
-// for a run starting at d0 a warp keeps the 16 older values P_{t-d0} .. in a register window and
-// slides it back one frame per delay, so one shared-memory load serves 16 pairs; an isolated
-// delay costs one load per pair.  The tile's slots stream newest-to-oldest through a 512-slot
-// ring in shared memory, filled by bulk asynchronous copies (TMA, cp.async.bulk) that complete on
-// mbarriers, one copy group per stage, the next stage's group prefetched while the current one
-// computes when both fit.  Per-warp partial sums go through shared memory, are added in a fixed
-// warp order and then into the Kahan (sum, compensation) pair of the accumulator.
+// Tiled kernel (variant 0).  One CTA owns a tile of 16 consecutive modes for a block of K = 512
+// new frames; 16 warps each take 32 consecutive frames, a half-warp 16 of them (lane = mode + 16 x
+// half), holding those 16 spectra in registers.  Delays are taken in order as runs of consecutive
+// values ("sub-runs" of up to 16): for a run starting at d0 a lane keeps the 16 older values
+// P_{t-d0} .. in a register window and slides it back one frame per delay, so one shared-memory
+// load serves 16 pairs; an isolated delay costs one load per pair.  The tile's slots (128 bytes:
+// 16 modes) stream newest-to-oldest through a 1024-slot ring in shared memory, filled by bulk
+// asynchronous copies (TMA, cp.async.bulk) that complete on mbarriers, one copy group per stage,
+// later stages' groups issued while earlier ones compute as far as the ring's rows allow (16-mode
+// slots give twice the rows of 32-mode ones in the same memory, hence the deeper prefetch that the
+// stages of sparse large delays need).  Per-lane partial sums go through shared memory, are added
+// in a fixed order and then into the Kahan (sum, compensation) pair of the accumulator.
 #include <algorithm>
 #include <cmath>
 
@@ -52,10 +54,10 @@ bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<Sub
         srs->push_back({j0, len, d0});
         j = j0 + len;
     }
-    // SPAN: the widest delay range of one stage (measured on GB300: 112 runs the 200 log delays
-    // 1..2000 2 % faster than 64; 128 slows lists of sparse large delays, whose copy groups then
-    // leave too few free slot rows to prefetch)
-    const int K = kDelayBlock, SB = kSlotBuf, SPAN = 112;
+    // SPAN: the widest delay range of one stage (measured on GB300 with K = 512 and 1024 slot
+    // rows: 240 runs the 200 log delays 1..2000 2 % faster than 112 and sparse delays 64 apart 9 %
+    // faster; 320 and more slow both, their copy groups leaving too few free rows to prefetch)
+    const int K = kDelayBlock, SB = kSlotBuf, SPAN = 240;
     // needed frame range of every consumer step, relative to t0: step 0 reads the block itself
     std::vector<int> need_lo(1, 0), need_hi(1, K - 1);
     // frames t0 + lo_prev .. are in the buffer after the block is loaded (a cross pass's block is
@@ -178,17 +180,18 @@ __device__ __forceinline__ unsigned long long global_ns()
 
 // ------------------------------------------------------------------ tiled kernel
 
-constexpr int kWarps = 16;                       // consumer warps (16 frames each)
-constexpr int kTw = 16;                          // consecutive frames per consumer warp
+constexpr int kWarps = 16;                       // consumer warps (32 frames each: 16 per half-warp)
+constexpr int kTw = 16;                          // consecutive frames per lane (a half-warp's run)
 constexpr int kProducer = kWarps;                // warp that issues the copy groups
 constexpr int kWriter = kWarps + 1;              // warp that reduces partial sums into the accumulators
 constexpr int kThreads = (kWarps + 2) * 32;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
-static_assert(kWarps * kTw == kDelayBlock, "block = warps x frames per warp");
+static_assert(kWarps * 2 * kTw == kDelayBlock, "block = warps x half-warps x frames per lane");
+static_assert(kTile == 16, "a half-warp covers one tile: lane = mode + 16 x half");
 
 struct TiledSmem {
-    float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf
-    float red[2][16][kWarps][kTile];       // per-warp partial sums of a batch of up to 16 delays, x2
+    float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf (128-byte rows)
+    float red[2][16][kWarps][32];          // per-lane partial sums of a batch of up to 16 delays, x2
     int jd[2][16];                         // delay indices of a batch
     int pend[2];                           // delays in a batch
     unsigned long long full[kFullBars];    // copy-group barriers (group g on full[g % kFullBars])
@@ -334,9 +337,9 @@ __device__ __forceinline__ float2 unpk(pk_t a)
 
 template <bool MASKED, bool WRAP, bool PACKED>
 __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int base, int len,
-                                       float (*red)[kWarps][kTile], int pend, int hi_lim)
+                                       float (*red)[kWarps][32], int pend, int hi_lim)
 {
-    const float2 *col = &S.buf[0][lane];
+    const float2 *col = &S.buf[0][lane & (kTile - 1)];
     const float2 *p0 = col + (size_t)((base & (kSlotBuf - 1)) * kTile);
     auto ldf = [&](int off) -> pk_t {  // the value of frame base + off
         const float2 *a = WRAP ? col + (size_t)(((base + off) & (kSlotBuf - 1)) * kTile) : p0 + off * kTile;
@@ -380,19 +383,22 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
     }
 }
 
-// Picks the sub-run variant for this warp (the choice is uniform within the warp).
+// Picks the sub-run variant for this warp (the choice is uniform within the warp).  Half-warp h
+// holds frames taw + 16 h .. taw + 16 h + 15 (ta: this lane's first frame, hi_lim: its count of
+// new frames); the conditions below hold for both halves at once.
 template <bool PACKED>
-__device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int ta,
-                                                int d0, int len, float (*red)[kWarps][kTile], int pend, int hi_lim)
+__device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int taw,
+                                                int ta, int d0, int len, float (*red)[kWarps][32], int pend,
+                                                int hi_lim, int hi_lim_w)
 {
-    const int base = ta - d0;
-    if (hi_lim <= 0 || base + kTw - 1 < 0) {  // no pair of this warp is valid
+    const int base = ta - d0, basew = taw - d0;
+    if (hi_lim_w <= 0 || basew + 2 * kTw - 1 < 0) {  // no pair of this warp is valid
         for (int u = 0; u < len; ++u) red[pend + u][warp][lane] = 0.f;
         return;
     }
-    if (base - (len - 1) >= 0 && hi_lim >= kTw) {
-        const int r0 = base & (kSlotBuf - 1);
-        if (r0 >= 16 && r0 + 15 < kSlotBuf)
+    if (basew - (len - 1) >= 0 && hi_lim_w >= 2 * kTw) {
+        const int r0 = basew & (kSlotBuf - 1);  // rows r0 - 15 .. r0 + 31 of both halves, unwrapped
+        if (r0 >= 16 && r0 + 2 * kTw - 1 < kSlotBuf)
             subrun<false, false, PACKED>(S, xt, lane, warp, base, len, red, pend, hi_lim);
         else
             subrun<false, true, PACKED>(S, xt, lane, warp, base, len, red, pend, hi_lim);
@@ -503,22 +509,25 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
             // After a failed wait the batch may not be written yet: stop touching global memory
             // (the launch's results are void and the error word says so).
             if (!wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err, 2, k)) break;
+            // lane = mode + 16 h: half h adds the batch's delays 8 h .. 8 h + 7 at its mode, the 16
+            // warps' two half-warp partials in a fixed order
             const int pend = S.pend[b];
-            float2 *base = acc + tile * kTile + lane;
-            float2 old[16];
-            int jd[16];
+            const int m = lane & (kTile - 1), jh = (lane >> 4) * 8;
+            float2 *base = acc + tile * kTile + m;
+            float2 old[8];
+            int jd[8];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                jd[j] = S.jd[b][j];
-                if (j < pend && (unsigned)jd[j] < (unsigned)nd) old[j] = base[(size_t)jd[j] * M];
+            for (int q = 0; q < 8; ++q) {
+                jd[q] = S.jd[b][jh + q];
+                if (jh + q < pend && (unsigned)jd[q] < (unsigned)nd) old[q] = base[(size_t)jd[q] * M];
             }
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                if (j < pend && (unsigned)jd[j] < (unsigned)nd) {
+            for (int q = 0; q < 8; ++q) {
+                if (jh + q < pend && (unsigned)jd[q] < (unsigned)nd) {
                     float s = 0.f;
 #pragma unroll
-                    for (int w = 0; w < kWarps; ++w) s += S.red[b][j][w][lane];
-                    base[(size_t)jd[j] * M] = kahan_add(old[j], s);
+                    for (int w = 0; w < kWarps; ++w) s += S.red[b][jh + q][w][m] + S.red[b][jh + q][w][m + kTile];
+                    base[(size_t)jd[q] * M] = kahan_add(old[q], s);
                 }
             }
             __syncwarp();
@@ -529,12 +538,15 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         }
     } else {
         // consumers
-        const int ta = (int)(t0 + (long long)warp * kTw);  // first frame of this warp (frame indices < 2^31)
-        const int hi_lim = (int)(t0 + nb - ta);             // frames ta + i are new frames for i < hi_lim
+        const int taw = (int)(t0 + (long long)warp * 2 * kTw);  // first frame of this warp (indices < 2^31)
+        const int ta = taw + (lane >> 4) * kTw;                 // first frame of this lane's half-warp
+        const int hi_lim = (int)(t0 + nb - ta);                 // frames ta + i are new frames for i < hi_lim
+        const int hi_lim_w = (int)(t0 + nb - taw);
         wait_group(S, 0, err);
         pk_t xt[kTw];
 #pragma unroll
-        for (int i = 0; i < kTw; ++i) xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane]);
+        for (int i = 0; i < kTw; ++i)
+            xt[i] = *reinterpret_cast<const pk_t *>(&S.buf[(ta + i) & (kSlotBuf - 1)][lane & (kTile - 1)]);
         step_done(S, lane);
 
         // After a failed wait the loop still runs to the end (every shared-memory index stays in
@@ -557,7 +569,8 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                     open_batch(batch);
                 }
                 if (tid < sr.len) S.jd[batch & 1][pend + tid] = sr.j0 + tid;
-                subrun_dispatch<PACKED>(S, xt, lane, warp, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim);
+                subrun_dispatch<PACKED>(S, xt, lane, warp, taw, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim,
+                                        hi_lim_w);
                 pend += sr.len;
             }
             step_done(S, lane);

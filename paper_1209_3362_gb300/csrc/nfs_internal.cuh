@@ -98,13 +98,15 @@ cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const
                            typename cplx_t<T>::type *ring, int R, int slot0, cudaStream_t s,
                            const typename cplx_t<T>::type *scratch = nullptr, const float2 *tws_col = nullptr);
 
-// Layout of the FP32 spectrum ring: tiles of 32 consecutive modes (flat k = ky * Wp + kx), each
-// tile holding its R slots contiguously, [tile][slot][32] float2, so the time series of a tile is
-// one contiguous run of memory (a slot range is one bulk copy).
-constexpr int kTile = 32;
+// Layout of the FP32 spectrum ring: tiles of 16 consecutive modes (flat k in column-major mode
+// order), each tile holding its R slots contiguously, [tile][slot][16] float2 (128-byte slots), so
+// the time series of a tile is one contiguous run of memory (a slot range is one bulk copy).
+constexpr int kTile = 16;
+constexpr int kTileShift = 4;
+static_assert((1 << kTileShift) == kTile, "tile shift");
 __host__ __device__ __forceinline__ size_t ring_index(int slot, size_t k, int R)
 {
-    return ((k >> 5) * (size_t)R + (size_t)slot) * kTile + (k & (kTile - 1));
+    return ((k >> kTileShift) * (size_t)R + (size_t)slot) * kTile + (k & (kTile - 1));
 }
 
 // Schedule of the tiled delay kernel (built on the host from the delay list, fixed per context).
@@ -121,10 +123,10 @@ struct Stage {
                      // this many steps (step 0 = reading the block's own frames, step s+1 = stage s):
                      // its slot-ring rows are then free and its mbarrier has been observed
 };
-constexpr int kFullBars = 4;       // copy-group mbarriers of the tiled kernel (group g uses g % 4)
+constexpr int kFullBars = 8;       // copy-group mbarriers of the tiled kernel (group g uses g % 8)
 constexpr int kDelayErrWords = 48; // status words of the tiled kernel
-constexpr int kDelayBlock = 256;   // K of the tiled kernel: 16 warps x 16 frames
-constexpr int kSlotBuf = 512;      // shared-memory slot ring of the tiled kernel (slots)
+constexpr int kDelayBlock = 512;   // K of the tiled kernel: 16 warps x 2 half-warps x 16 frames
+constexpr int kSlotBuf = 1024;     // shared-memory slot ring of the tiled kernel (128-byte slots)
 // cross: a cross pass (the block's frames belong to one sequence, the older frames of every pair
 // to another, indexed alike; delay 0 is a real pair), see DelayArgs::ring_cur
 bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *subruns,
