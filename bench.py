@@ -55,8 +55,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "4424f195d80ef0a94dd8302d55453008a46d040c8dd8ba67c9ef6892c1477929",
-                         "dram_bytes_per_alg_byte": 0.9963}
+NCU_DELAY_CALIBRATION = {"sha256": "d7202163caaf84dad59a33505bab6f2c82875547a93dbf6e35bedda477a23077",
+                         "dram_bytes_per_alg_byte": 0.9961}
 
 
 def delay_kernel_sha():

@@ -189,14 +189,17 @@ constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 static_assert(kWarps * 2 * kTw == kDelayBlock, "block = warps x half-warps x frames per lane");
 static_assert(kTile == 16, "a half-warp covers one tile: lane = mode + 16 x half");
 
+constexpr int kRedBufs = 3;                      // partial-sum buffers: the writer may lag two batches
+constexpr int kRedStride = kWarps * 32 + 2;      // words per delay slot of a buffer (the +2 puts the
+                                                 // writer's two half-warps, 8 slots apart, on
+                                                 // different banks)
+
 struct TiledSmem {
-    float2 buf[kSlotBuf][kTile];          // slot ring: frame s at row s mod kSlotBuf (128-byte rows)
-    float red[2][16][kWarps][32];          // per-lane partial sums of a batch of up to 16 delays, x2
-    int jd[2][16];                         // delay indices of a batch
-    int pend[2];                           // delays in a batch
-    unsigned long long full[kFullBars];    // copy-group barriers (group g on full[g % kFullBars])
-    unsigned long long red_full[2];        // batch written by all consumer warps
-    unsigned long long red_free[2];        // batch drained by the writer
+    float2 buf[kSlotBuf][kTile];            // slot ring: frame s at row s mod kSlotBuf (128-byte rows)
+    float red[kRedBufs][16][kRedStride];     // per-lane partial sums of a batch of up to 16 delays
+    unsigned long long full[kFullBars];      // copy-group barriers (group g on full[g % kFullBars])
+    unsigned long long red_full[kRedBufs];   // batch k (buffer k % 3) written by all consumer warps
+    unsigned long long red_free[kRedBufs];   // batch k drained by the writer
     int done;                              // consumer-warp step completions, all warps (diagnostics)
     int abort;                             // set when a bounded wait gives up
     int wsteps[kWarps];                    // per consumer warp: steps completed (the producer waits for
@@ -337,7 +340,7 @@ __device__ __forceinline__ float2 unpk(pk_t a)
 
 template <bool MASKED, bool WRAP, bool PACKED>
 __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int base, int len,
-                                       float (*red)[kWarps][32], int pend, int hi_lim)
+                                       float (*red)[kRedStride], int pend, int hi_lim)
 {
     const float2 *col = &S.buf[0][lane & (kTile - 1)];
     const float2 *p0 = col + (size_t)((base & (kSlotBuf - 1)) * kTile);
@@ -362,7 +365,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                 }
                 a[i & 3] = psq_acc(d, a[i & 3]);
             }
-            red[pend + uu][warp][lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
+            red[pend + uu][warp * 32 + lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
         } else {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -377,7 +380,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                 a[i & 3] = fmaf(dr, dr, a[i & 3]);
                 a[i & 3] = fmaf(di, di, a[i & 3]);
             }
-            red[pend + uu][warp][lane] = (a[0] + a[1]) + (a[2] + a[3]);
+            red[pend + uu][warp * 32 + lane] = (a[0] + a[1]) + (a[2] + a[3]);
         }
         if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = ldf(-uu - 1);
     }
@@ -388,12 +391,12 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
 // new frames); the conditions below hold for both halves at once.
 template <bool PACKED>
 __device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int taw,
-                                                int ta, int d0, int len, float (*red)[kWarps][32], int pend,
+                                                int ta, int d0, int len, float (*red)[kRedStride], int pend,
                                                 int hi_lim, int hi_lim_w)
 {
     const int base = ta - d0, basew = taw - d0;
     if (hi_lim_w <= 0 || basew + 2 * kTw - 1 < 0) {  // no pair of this warp is valid
-        for (int u = 0; u < len; ++u) red[pend + u][warp][lane] = 0.f;
+        for (int u = 0; u < len; ++u) red[pend + u][warp * 32 + lane] = 0.f;
         return;
     }
     if (basew - (len - 1) >= 0 && hi_lim_w >= 2 * kTw) {
@@ -436,7 +439,7 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
 
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_init(&S.full[b], 1);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kRedBufs; ++b) {
             mbar_init(&S.red_full[b], kWarps);
             mbar_init(&S.red_free[b], 1);
         }
@@ -444,10 +447,6 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         S.abort = 0;
         S.wdrained = 0;
         for (int w = 0; w < kWarps; ++w) S.wsteps[w] = S.wbatches[w] = 0;
-        for (int b = 0; b < 2; ++b) {
-            S.pend[b] = 0;
-            for (int j = 0; j < 16; ++j) S.jd[b][j] = 0;
-        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -503,31 +502,44 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
             }
         }
     } else if (warp == kWriter) {
-        // reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs
+        // Reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs.
+        // A batch is the longest run of consecutive sub-runs with at most 16 delays (the consumers'
+        // rule), so the writer takes every batch's delays from the schedule.  (Loading the next
+        // batch's accumulators right after releasing a buffer measured slower on runs of
+        // consecutive delays than loading them once the batch is written.)
+        // lane = mode + 16 h: half h adds the batch's delays 8 h .. 8 h + 7 at its mode.
+        const int m = lane & (kTile - 1), jh = (lane >> 4) * 8;
+        float2 *const base = acc + tile * kTile + m;
+        const int nsr = nst > 0 ? sched.st[nst - 1].sr0 + sched.st[nst - 1].nsr : 0;
+        int r = 0, jb = 0, n = 0;
+        auto next_batch = [&]() {  // the delays jb .. jb+n-1 of the batch starting at sub-run r
+            jb = sched.sr[r].j0;
+            n = 0;
+            while (r < nsr && n + sched.sr[r].len <= 16) n += sched.sr[r++].len;
+        };
+        float2 old[8];
+        auto load_old = [&]() {
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (jh + q < n && (unsigned)(jb + jh + q) < (unsigned)nd) old[q] = base[(size_t)(jb + jh + q) * M];
+        };
         for (int k = 0; k < nbatch; ++k) {
-            const int b = k & 1;
+            const int b = k % kRedBufs;
             // After a failed wait the batch may not be written yet: stop touching global memory
             // (the launch's results are void and the error word says so).
-            if (!wait_bar(S, &S.red_full[b], (unsigned)((k >> 1) & 1), err, 2, k)) break;
-            // lane = mode + 16 h: half h adds the batch's delays 8 h .. 8 h + 7 at its mode, the 16
-            // warps' two half-warp partials in a fixed order
-            const int pend = S.pend[b];
-            const int m = lane & (kTile - 1), jh = (lane >> 4) * 8;
-            float2 *base = acc + tile * kTile + m;
-            float2 old[8];
-            int jd[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                jd[q] = S.jd[b][jh + q];
-                if (jh + q < pend && (unsigned)jd[q] < (unsigned)nd) old[q] = base[(size_t)jd[q] * M];
+            if (!wait_bar(S, &S.red_full[b], (unsigned)((k / kRedBufs) & 1), err, 2, k)) break;
+            if (r < nsr) {
+                next_batch();
+                load_old();
             }
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                if (jh + q < pend && (unsigned)jd[q] < (unsigned)nd) {
-                    float s = 0.f;
+                if (jh + q < n && (unsigned)(jb + jh + q) < (unsigned)nd) {
+                    const float *row = S.red[b][jh + q];
+                    float sum = 0.f;
 #pragma unroll
-                    for (int w = 0; w < kWarps; ++w) s += S.red[b][jh + q][w][m] + S.red[b][jh + q][w][m + kTile];
-                    base[(size_t)jd[q] * M] = kahan_add(old[q], s);
+                    for (int w = 0; w < kWarps; ++w) sum += row[w * 32 + m] + row[w * 32 + m + kTile];
+                    base[(size_t)(jb + jh + q) * M] = kahan_add(old[q], sum);
                 }
             }
             __syncwarp();
@@ -552,8 +564,9 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         // After a failed wait the loop still runs to the end (every shared-memory index stays in
         // bounds, the numbers are wrong and the error word says so), so no barrier loses a warp.
         int pend = 0, batch = 0;
-        auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 2
-            if (k >= 2) wait_bar(S, &S.red_free[k & 1], (unsigned)(((k - 2) >> 1) & 1), err, 3, k);
+        auto open_batch = [&](int k) {  // before writing batch k: the writer has drained batch k - 3
+            if (k >= kRedBufs)
+                wait_bar(S, &S.red_free[k % kRedBufs], (unsigned)(((k - kRedBufs) / kRedBufs) & 1), err, 3, k);
         };
         open_batch(0);
         for (int s = 0; s < nst; ++s) {
@@ -562,28 +575,25 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
             for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
                 const SubRun sr = sched.sr[r];
                 if (pend + sr.len > 16) {
-                    if (tid == 0) S.pend[batch & 1] = pend;
-                    hand_over(S, batch & 1, lane);
+                    hand_over(S, batch % kRedBufs, lane);
                     ++batch;
                     pend = 0;
                     open_batch(batch);
                 }
-                if (tid < sr.len) S.jd[batch & 1][pend + tid] = sr.j0 + tid;
-                subrun_dispatch<PACKED>(S, xt, lane, warp, taw, ta, sr.d0, sr.len, S.red[batch & 1], pend, hi_lim,
+                subrun_dispatch<PACKED>(S, xt, lane, warp, taw, ta, sr.d0, sr.len, S.red[batch % kRedBufs], pend, hi_lim,
                                         hi_lim_w);
                 pend += sr.len;
             }
             step_done(S, lane);
         }
         if (pend) {
-            if (tid == 0) S.pend[batch & 1] = pend;
-            hand_over(S, batch & 1, lane);
+            hand_over(S, batch % kRedBufs, lane);
         }
     }
     __syncthreads();  // every role has finished this tile (all copies issued were consumed)
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_inval(&S.full[b]);
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kRedBufs; ++b) {
             mbar_inval(&S.red_full[b]);
             mbar_inval(&S.red_free[b]);
         }
