@@ -71,7 +71,7 @@ int nfs_create(int H, int W, const int32_t *delays, int n_delays, int n_qbins, n
 
 /*
  * Same as nfs_create with an explicit path (NFS_PATH_*) and block size K (frames per fused delay
- * update, 1..256; 0 = the default 256).  The plain FP64 path ignores K (it updates once per frame).
+ * update, 1..512; 0 = the default 512).  The plain FP64 path ignores K (it updates once per frame).
  */
 int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block_frames,
                   nfs_ctx **out);
@@ -245,13 +245,13 @@ int nfs_fit_gauss_newton(const float *D, const float *tau, int n_delays, int n_b
  * paper re-uploads images through a FIFO, diagonal by diagonal).  Here the delays are split into
  * bands that each fit a budget of max_ring_slots spectra, and every band is one pass over the
  * frames, which stay in host memory:
- *   - band 0: an ordinary pass over the delays d with d + 256 <= max_ring_slots (one transform per
- *     frame);
- *   - a later band with smallest delay lo: a pass with shift s = 256 floor(lo / 256) that pairs
+ *   - band 0: an ordinary pass over the delays d with d + K <= max_ring_slots, K = 512 the block
+ *     of the fused update (one transform per frame);
+ *   - a later band with smallest delay lo: a pass with shift s = K floor(lo / K) that pairs
  *     frame u + s (as the newer frame) with frame u + s - d, holding the frames u + s in a
- *     256-slot ring and the frames u in a ring of (largest d - s) + 256 slots (two transforms per
- *     frame index: N - s each); its delays d satisfy (d - s) + 512 <= max_ring_slots.
- * Every pair is added in the same 256-frame block and in the same order as in one in-core pass,
+ *     K-slot ring and the frames u in a ring of (largest d - s) + K slots (two transforms per
+ *     frame index: N - s each); its delays d satisfy (d - s) + 2 K <= max_ring_slots.
+ * Every pair is added in the same K-frame block and in the same order as in one in-core pass,
  * so the results equal those of nfs_create + nfs_push_frames + nfs_structure_function.
  *
  * nfs_out_of_core_plan() gives the bands without touching the GPU (host logic only):
@@ -260,8 +260,9 @@ int nfs_fit_gauss_newton(const float *D, const float *tau, int n_delays, int n_b
  *   n_bands, n_transforms   out: the number of bands and of frame transforms all passes make
  *                (N per ordinary band, 2 (N - s) per shifted band; the paper's FIFO scheme makes
  *                N (2 alpha - 3 + 2 / alpha) for N - 1 = alpha N* frames and a memory of N*)
- * Arrays sized for n_delays bands suffice.  NFS_EINVAL for budgets below 768 slots (a band must
- * hold its first delay) or bad delays; NFS_EUNSUPPORTED if one delay alone exceeds the schedule.
+ * Arrays sized for n_delays bands suffice.  NFS_EINVAL for budgets below 3 K = 1536 slots (a band
+ * must hold its first delay) or bad delays; NFS_EUNSUPPORTED if one delay alone exceeds the
+ * schedule.
  *
  * nfs_structure_function_out_of_core() runs the bands and returns, for the whole delay list, what
  * nfs_structure_function returns (FP32 fused path).  frames: HOST memory [n_frames][H][W] uint16
