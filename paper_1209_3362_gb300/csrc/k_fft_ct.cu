@@ -198,8 +198,21 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
             const int j = jj[p], b = bb[p];
             const int k = j % NS;
             if (NS > 1) {
+                // powers of two of the twiddle are read from the table, the others are their
+                // products (w^3 = w^2 w, w^5 = w^4 w, ...): fewer L1 reads, a few roundings more
+                float2 tw[R];
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], __ldg(tws + OFF + (r - 1) * NS + k));
+                for (int r = 1; r < R; ++r) {
+                    if ((r & (r - 1)) == 0) {
+                        tw[r] = __ldg(tws + OFF + (r - 1) * NS + k);
+                    } else {
+                        int hb = 1;
+                        while (2 * hb <= r) hb *= 2;
+                        tw[r] = cmul(tw[hb], tw[r - hb]);
+                    }
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], tw[r]);
             }
             Dft<R>::run(v[p]);
             const int base = (j / NS) * NS * R + k;
