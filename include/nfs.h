@@ -180,7 +180,7 @@ int64_t nfs_launch_count(const nfs_ctx *ctx);
  * Many independent sequences (regions of interest, cameras, experiments) of uneven frame shapes
  * and delay lists analysed together: each member is a context of its own, all members share one
  * stream, and the delay update of every member whose block of K frames is complete runs in ONE
- * persistent launch over a ragged work list of (sequence, 32-mode tile) items.  The FFT launch
+ * persistent launch over a ragged work list of (sequence, 16-mode tile) items.  The FFT launch
  * size of each frame shape is chosen by a measuring autotuner when the batch is created.
  */
 typedef struct nfs_batch nfs_batch;

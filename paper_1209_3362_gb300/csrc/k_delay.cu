@@ -425,7 +425,7 @@ __device__ __forceinline__ void mbar_inval(unsigned long long *bar)
     asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// One CTA's pass over one 32-mode tile for a block of new frames t0 .. t0+nb-1 (all warps of the
+// One CTA's pass over one 16-mode tile for a block of new frames t0 .. t0+nb-1 (all warps of the
 // CTA take part; every role falls through to the final barrier, so a persistent caller can run
 // several tiles in a row).  sched: the sequence's schedule (kernel parameters or global memory);
 // nst, nbatch: its stages and batches for this block (early blocks leave late stages out).

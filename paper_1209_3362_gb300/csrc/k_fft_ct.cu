@@ -8,7 +8,7 @@
 // warp's load is one contiguous run); shared memory is padded by one element in 16 so the
 // strided stores of the early Stockham stages do not collide in banks.  The row pass
 // writes the column-pair scratch, which the column pass reads as one contiguous run per CTA; the
-// column pass (in place in one buffer) writes each column as whole 32-mode tile rows of the ring.
+// column pass (in place in one buffer) writes each column as whole 16-mode tile rows of the ring.
 #include <cmath>
 
 #include "nfs_internal.cuh"
