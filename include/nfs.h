@@ -141,8 +141,8 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 #define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K (FP32) or tau_max + 64 (FP64) */
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
 #define NFS_OPT_PATH 5         /* read-only: NFS_PATH_* */
-#define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..16 FP32, 1..64 FP64; default 4;
-                                  0 = choose by measurement, FP32 path) */
+#define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..32 FP32, 1..64 FP64; default 32
+                                  FP32, 4 FP64; 0 = choose by measurement, FP32 path) */
 #define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel: 0 = tiled, packed f32x2 math (default);
                                    1 = one thread per mode; 2 = tiled, scalar FP32 math */
 #define NFS_OPT_FFT_GENERIC 8   /* 1 = generic FFT kernels even where size-specialised ones exist */

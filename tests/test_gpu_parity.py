@@ -247,7 +247,7 @@ def test_specialised_and_generic_fft_agree_at_2048(oracle_lib):
 
 
 def test_full_size_2048_sampled_modes(oracle_lib):
-    """2048x2048 frames in the launch configuration the benchmark times (512-frame blocks, 4-frame
+    """2048x2048 frames in the launch configuration the benchmark times (512-frame blocks, 32-frame
     FFT launches, steady-state blocks after tau_max): sampled modes of the exported 2-D spectra
     against the oracle's one-mode definition (real-space differences, one DFT coefficient), and
     the binned D against an FP64 re-binning of the exported spectra with the oracle's bin table."""
@@ -258,7 +258,7 @@ def test_full_size_2048_sampled_modes(oracle_lib):
     fr = S.OUFrameSource(H, W, 1.0, gamma0=0.01, seed=81, device="cuda", dtype=torch.float32).frames_numpy(N)
     with P.NFS(H, W, delays, nq) as ctx:
         K = ctx.get_option(P.OPT_BLOCK_FRAMES)
-        assert K == 512 and ctx.get_option(P.OPT_FFT_CHUNK) == 4 and N >= delays[-1] + K  # a steady block
+        assert K == 512 and ctx.get_option(P.OPT_FFT_CHUNK) == 32 and N >= delays[-1] + K  # a steady block
         ctx.push_frames_device(torch.from_numpy(fr.view(np.int16)).cuda())
         got = ctx.structure_function()
         spectra = {j: ctx.export_spectrum(j) for j in (0, 1, 4, 6)}
