@@ -55,8 +55,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "d7202163caaf84dad59a33505bab6f2c82875547a93dbf6e35bedda477a23077",
-                         "dram_bytes_per_alg_byte": 0.9961}
+NCU_DELAY_CALIBRATION = {"sha256": "e2455f50f916bfbe89fb5babe8b5c44ceafaf7829b1aef81e4c3afc7ca4d8cc4",
+                         "dram_bytes_per_alg_byte": 0.9964}
 
 
 def delay_kernel_sha():
