@@ -220,7 +220,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS) + sorted(S.RAGGED_WORKLOADS))
+    ap.add_argument("--workload", default="ddm2048", choices=sorted(S.WORKLOADS) + sorted(S.RAGGED_WORKLOADS) + sorted(S.ROI_WORKLOADS))
     ap.add_argument("--frames", type=int, default=0, help="override N (smaller runs; not a bench value)")
     ap.add_argument("--H", type=int, default=0, help="override frame height (profiling cases; not a bench value)")
     ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
@@ -234,6 +234,8 @@ def main():
     args = ap.parse_args()
     if args.workload in S.RAGGED_WORKLOADS:
         return run_ragged(args, S.RAGGED_WORKLOADS[args.workload])
+    if args.workload in S.ROI_WORKLOADS:
+        return run_roi(args, S.ROI_WORKLOADS[args.workload])
     w = S.WORKLOADS[args.workload]
     if args.frames or args.H or args.W or args.delays:
         import dataclasses
@@ -479,6 +481,56 @@ def run_ragged(args, rw):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": rw.name, "sequences": rw.n_seq, "frames_per_sequence": rw.N, "shapes": shapes,
                        "delays": 64, "tau_max": rw.N // 2},
+            "gpu_launches": int(b.launch_count - l0), "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    b.close()
+
+
+def run_roi(args, rw):
+    """Regions of interest: full camera frames resident in HBM, cut into a grid of windows by the
+    library (nfs_roi_push_device), every window analysed as a sequence of its own."""
+    import torch
+    import paper_1209_3362_gb300 as P
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    P.build()
+    P.load_library()
+    src = S.OUFrameSource(rw.H, rw.W, rw.Dc, seed=rw.seed, device="cuda", dtype=torch.float32)
+    frames = torch.empty((rw.N, rw.H, rw.W), dtype=torch.int16, device="cuda")
+    for o in range(0, rw.N, 50):
+        frames[o:o + 50] = src.next_frames(min(50, rw.N - o))
+    torch.cuda.synchronize()
+    rois = rw.rois()
+    b = P.NFSRoi(rw.H, rw.W, rois, rw.delays, rw.n_qbins)
+    stream = torch.cuda.ExternalStream(b.stream)
+
+    def step():
+        b.reset()
+        b.push_frames_device(frames)
+        return [b.structure_function(r) for r in range(len(rois))]
+
+    for _ in range(max(args.warmup, 0)):
+        step()
+    l0 = b.launch_count
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        ev1.synchronize()
+        wall = time.perf_counter() - t0
+    step_ms = max(ev0.elapsed_time(ev1), 1000.0 * wall) / args.steps
+    h, w = rois[0][2], rois[0][3]
+    line = {"metric": f"frames/s, {rw.H}x{rw.W} frames cut into {len(rois)} regions of interest of {h}x{w}",
+            "value": rw.N / (step_ms / 1000.0), "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": rw.name, "frames": rw.N, "H": rw.H, "W": rw.W, "rois": len(rois),
+                       "roi_shape": [h, w], "delays": len(rw.delays), "tau_max": rw.delays[-1],
+                       "n_qbins": rw.n_qbins},
             "gpu_launches": int(b.launch_count - l0), "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     b.close()

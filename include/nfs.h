@@ -209,6 +209,32 @@ int64_t nfs_batch_launch_count(const nfs_batch *b);
 const char *nfs_batch_last_error(const nfs_batch *b);
 
 /*
+ * ---------------------------------------------------------------- regions of interest
+ * Spatially resolved analysis (near-field scattering lends itself to experiments that resolve the
+ * sample in space; paper, introduction).  Each frame of
+ * one H x W camera sequence is cut into n_roi windows, and window r (rows y0[r] .. y0[r]+h[r],
+ * columns x0[r] .. x0[r]+w[r]) is analysed as a sequence of its own: normalised by its own spatial
+ * mean, transformed at h[r] x w[r], binned into n_qbins[r] bins, with the same delay list for every
+ * window.  Windows may overlap.  The result is a batch (above) with one member per window:
+ * read window r with nfs_batch_structure_function(b, r, ...); nfs_batch_reset and
+ * nfs_batch_destroy apply.  Window r's result equals nfs_create(h[r], w[r], ...) fed the cropped
+ * frames, bit for bit.
+ *
+ * nfs_roi_create: NFS_EINVAL for a window outside the frame, an odd W, x0 or w (the crop moves
+ * 4-byte words), an empty list, a NULL pointer or a delay list or bin count nfs_create rejects;
+ * NFS_EUNSUPPORTED for a window shape nfs_create rejects (all checked before any CUDA call);
+ * NFS_ENOMEM.
+ * nfs_roi_push: n_frames full frames [n][H][W] from host memory; the buffer may be reused on
+ * return.  nfs_roi_push_device: full frames already on the device, 4-byte aligned, read by
+ * stream-ordered kernels on the batch's stream (keep them alive until nfs_batch_synchronize).
+ * Both: NFS_EINVAL for a batch not made by nfs_roi_create; sticky errors as nfs_push_frames.
+ */
+int nfs_roi_create(int H, int W, int n_roi, const int *y0, const int *x0, const int *h, const int *w,
+                   const int32_t *delays, int n_delays, const int *n_qbins, nfs_batch **out);
+int nfs_roi_push(nfs_batch *b, const uint16_t *host_frames, int n_frames);
+int nfs_roi_push_device(nfs_batch *b, const uint16_t *dev_frames, int n_frames);
+
+/*
  * ---------------------------------------------------------------- Eq. 1 fit
  * Per radial bin b, fit D_b(tau) = 2 A_b [1 - exp(-Gamma_b tau)] + 2 B_b to the structure function,
  * i.e. Eq. 1 with the intermediate scattering function f = exp(-Gamma tau), A = a T I_s (static

@@ -247,6 +247,31 @@ class RaggedWorkload:
 RAGGED_WORKLOADS = {"ragged48": RaggedWorkload("ragged48", 48, 500, 12093367)}
 
 
+@dataclasses.dataclass(frozen=True)
+class RoiWorkload:
+    """One camera sequence cut into a grid of equal regions of interest (spatially resolved
+    analysis): every window is analysed as a sequence of its own, with one delay list."""
+
+    name: str
+    H: int
+    W: int
+    N: int
+    grid: tuple  # (rows, cols) of windows
+    delays: tuple
+    n_qbins: int  # per window
+    Dc: float
+    seed: int
+
+    def rois(self):
+        """[(y0, x0, h, w)] row by row."""
+        h, w = self.H // self.grid[0], self.W // self.grid[1]
+        return [(r * h, c * w, h, w) for r in range(self.grid[0]) for c in range(self.grid[1])]
+
+
+ROI_WORKLOADS = {"roi2048": RoiWorkload("roi2048", 2048, 2048, 1000, (4, 4), tuple(log_delays(1, 500, 100)), 256,
+                                        2.0, 12093369)}
+
+
 def ragged_shapes(n_seq: int, seed: int) -> Sequence[tuple]:
     """Frame shapes for a ragged batch, drawn uniformly from the six camera ROI shapes."""
     shapes = [(128, 128), (256, 256), (384, 512), (512, 512), (768, 1024), (1024, 1024)]

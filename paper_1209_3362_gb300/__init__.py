@@ -103,6 +103,9 @@ def load_library(path: Optional[str] = None):
         "nfs_batch_get_stream": (V, [V]),
         "nfs_batch_launch_count": (I64, [V]),
         "nfs_batch_last_error": (ctypes.c_char_p, [V]),
+        "nfs_roi_create": (I, [I, I, I, V, V, V, V, V, I, V, PP]),
+        "nfs_roi_push": (I, [V, V, I]),
+        "nfs_roi_push_device": (I, [V, V, I]),
         "nfs_fit_loss_grad": (I, [V, V, I, I, V, V, V, V, V, V, V, V]),
         "nfs_fit_gauss_newton": (I, [V, V, I, I, V, V, V, I, ctypes.c_float, V]),
     }
@@ -426,3 +429,39 @@ class NFSBatch:
         if rc != NFS_OK:
             raise NFSError(rc, "nfs_get_option")
         return int(v.value)
+
+
+class NFSRoi(NFSBatch):
+    """Regions of interest of one camera sequence (nfs_roi_*): window r = (y0, x0, h, w) of every
+    H x W frame is analysed as a sequence of its own; structure_function(r) gives its result."""
+
+    def __init__(self, H, W, rois, delays, n_qbins):
+        self._L = load_library()
+        self.H, self.W = int(H), int(W)
+        self.rois = [tuple(int(v) for v in r) for r in rois]
+        n = len(self.rois)
+        self.shapes = [(h, w) for _, _, h, w in self.rois]
+        d = np.ascontiguousarray(np.asarray(delays, np.int32))
+        self.delays = [d] * n
+        self.n_qbins = [int(q) for q in (n_qbins if np.ndim(n_qbins) else [n_qbins] * n)]
+        assert len(self.n_qbins) == n
+        y0, x0, h, w = (np.array([r[i] for r in self.rois], np.int32) for i in range(4))
+        nq = np.array(self.n_qbins, np.int32)
+        hdl = ctypes.c_void_p()
+        rc = self._L.nfs_roi_create(self.H, self.W, n, _ptr(y0), _ptr(x0), _ptr(h), _ptr(w), _ptr(d), d.size,
+                                    _ptr(nq), ctypes.byref(hdl))
+        if rc != NFS_OK:
+            raise NFSError(rc, "nfs_roi_create")
+        self._h = hdl
+
+    def push_frames(self, frames):
+        """frames: [n, H, W] full frames in host memory."""
+        a = np.ascontiguousarray(frames, dtype=np.uint16)
+        assert a.shape[1:] == (self.H, self.W)
+        self._check(self._L.nfs_roi_push(self._h, _ptr(a), a.shape[0]), "nfs_roi_push")
+
+    def push_frames_device(self, frames):
+        """frames: CUDA tensor [n, H, W] of 2-byte integers (full frames)."""
+        assert tuple(frames.shape[1:]) == (self.H, self.W) and frames.is_contiguous()
+        self._check(self._L.nfs_roi_push_device(self._h, ctypes.c_void_p(frames.data_ptr()), frames.shape[0]),
+                    "nfs_roi_push_device")

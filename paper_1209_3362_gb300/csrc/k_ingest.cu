@@ -1,7 +1,10 @@
 // Ingest kernels: the exact spatial sum of every frame (for the mean normalisation of the
 // differential analysis: images are divided by their spatial average) and the FP32 reference
 // image subtracted before the FP32 transform.
+#include <algorithm>
+
 #include "nfs_internal.cuh"
+#include "roi.cuh"
 
 namespace nfs {
 
@@ -74,6 +77,40 @@ cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *s
     int bx = (int)((g.HW + 255) / 256);
     if (bx > 1216) bx = 1216;
     k_reference<<<bx, 256, 0, s>>>(frame0, sum0, g.HW, ref);
+    return cudaGetLastError();
+}
+
+
+// Regions of interest: window r of frame f goes to dst + roi[r].dst + f*h*w, row-major (a plain
+// crop; every window is then analysed as a sequence of its own).  One grid row per window, 4-byte
+// copies: W, x0 and w are even and src is 4-byte aligned, so every source and destination word is
+// whole.  32-bit indices: n*h*(w/2) < 2^31 is checked by the host.
+__global__ void __launch_bounds__(256) k_roi_crop(const uint16_t *__restrict__ src, int H, int W, int n,
+                                                  const RoiRect *__restrict__ roi, uint16_t *__restrict__ dst)
+{
+    const RoiRect r = roi[blockIdx.y];
+    const unsigned ww = (unsigned)r.w >> 1;  // words per window row
+    const unsigned rows = (unsigned)n * (unsigned)r.h;
+    const unsigned words = rows * ww;
+    const uint32_t *s32 = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d32 = reinterpret_cast<uint32_t *>(dst + r.dst);
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
+        const unsigned row = i / ww, xw = i - row * ww;
+        const unsigned f = row / (unsigned)r.h, y = row - f * (unsigned)r.h;
+        const size_t at = ((size_t)f * H + r.y0 + y) * (size_t)W + r.x0;  // even
+        d32[i] = __ldg(s32 + at / 2 + xw);
+    }
+}
+
+cudaError_t launch_roi_crop(const uint16_t *src, int H, int W, int n, const RoiRect *d_roi, int n_roi,
+                            long long max_words, int n_sm, uint16_t *dst, cudaStream_t s)
+{
+    if (n <= 0 || n_roi <= 0) return cudaSuccess;
+    long long bx = (max_words + 255) / 256;
+    const long long cap = std::max(1LL, (long long)n_sm * 8 / n_roi);
+    if (bx > cap) bx = cap;
+    if (bx < 1) bx = 1;
+    k_roi_crop<<<dim3((unsigned)bx, (unsigned)n_roi), 256, 0, s>>>(src, H, W, n, d_roi, dst);
     return cudaGetLastError();
 }
 

@@ -10,6 +10,7 @@
 #include <new>
 
 #include "nfs_internal.cuh"
+#include "roi.cuh"
 
 using namespace nfs;
 
@@ -504,12 +505,9 @@ int enter(nfs_ctx *c)
     return c->err;
 }
 
-int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
-                bool cross = false)
+// The argument checks of nfs_create_ex, made before any CUDA call.
+int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block)
 {
-    if (!out) return NFS_EINVAL;
-    if (cross && path != NFS_PATH_FUSED_F32) return NFS_EINVAL;
-    *out = nullptr;
     if (!delays || n_delays <= 0 || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
     if (path != NFS_PATH_FUSED_F32 && path != NFS_PATH_PLAIN_F64) return NFS_EINVAL;
     if (block < 0 || block > kMaxBlock) return NFS_EINVAL;
@@ -519,6 +517,17 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     }
     if (H < 2 || W < 2 || H > kMaxDim || W > kMaxDim || (H % 2) || (W % 2) || !factors_2_3(H) || !factors_2_3(W / 2))
         return NFS_EUNSUPPORTED;
+    return NFS_OK;
+}
+
+int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
+                bool cross = false)
+{
+    if (!out) return NFS_EINVAL;
+    if (cross && path != NFS_PATH_FUSED_F32) return NFS_EINVAL;
+    *out = nullptr;
+    const int rc_args = check_args(H, W, delays, n_delays, n_qbins, path, block);
+    if (rc_args) return rc_args;
 
     nfs_ctx *c = new (std::nothrow) nfs_ctx();
     if (!c) return NFS_ENOMEM;
@@ -961,6 +970,13 @@ struct nfs_batch {
     int err = NFS_OK;
     std::string errmsg;
     long long launches = 0;
+    // regions of interest (nfs_roi_create): windows of one H x W camera sequence
+    int roi_H = 0, roi_W = 0;
+    std::vector<RoiRect> rois;
+    RoiRect *d_rois = nullptr;
+    uint16_t *d_crop = nullptr;   // kRoiGroup frames of every window
+    uint16_t *d_full = nullptr;   // kRoiGroup full frames (host pushes), allocated on first use
+    long long roi_max_words = 0;  // 4-byte words of the largest window's group
 };
 
 static void batch_free(nfs_batch *b)
@@ -973,6 +989,9 @@ static void batch_free(nfs_batch *b)
     cudaFree(b->d_scheds);
     cudaFree(b->d_items);
     cudaFree(b->d_err);
+    cudaFree(b->d_rois);
+    cudaFree(b->d_crop);
+    cudaFree(b->d_full);
     if (b->stream) cudaStreamDestroy(b->stream);
     if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
     delete b;
@@ -1202,6 +1221,118 @@ int64_t nfs_batch_launch_count(const nfs_batch *b)
 }
 
 const char *nfs_batch_last_error(const nfs_batch *b) { return b ? b->errmsg.c_str() : ""; }
+
+// ---------------------------------------------------------------- regions of interest
+
+// Frames cropped per launch: kRoiGroup frames of every window are cut from the full frames in one
+// launch and pushed to the members as one device push.
+constexpr int kRoiGroup = 64;
+
+int nfs_roi_create(int H, int W, int n_roi, const int *y0, const int *x0, const int *h, const int *w,
+                   const int32_t *delays, int n_delays, const int *n_qbins, nfs_batch **out)
+{
+    if (!out) return NFS_EINVAL;
+    *out = nullptr;
+    if (H <= 0 || W <= 0 || (W & 1) || n_roi <= 0 || !y0 || !x0 || !h || !w || !delays || n_delays <= 0 ||
+        !n_qbins)
+        return NFS_EINVAL;
+    std::vector<RoiRect> rois((size_t)n_roi);
+    long long off = 0, max_words = 0;
+    for (int r = 0; r < n_roi; ++r) {
+        if (y0[r] < 0 || x0[r] < 0 || h[r] <= 0 || w[r] <= 0 || (x0[r] & 1) || (w[r] & 1) || y0[r] > H - h[r] ||
+            x0[r] > W - w[r])
+            return NFS_EINVAL;
+        const long long words = (long long)kRoiGroup * h[r] * (w[r] / 2);
+        if (words >= (1LL << 31)) return NFS_EINVAL;  // the crop kernel's 32-bit indices
+        const int rc_args = check_args(h[r], w[r], delays, n_delays, n_qbins[r], NFS_PATH_FUSED_F32, 0);
+        if (rc_args) return rc_args;
+        rois[(size_t)r] = RoiRect{y0[r], x0[r], h[r], w[r], off};
+        off += (2 * words + 127) / 128 * 128;  // each window's frames start 256-byte aligned
+        max_words = std::max(max_words, words);
+    }
+    std::vector<int> Hs((size_t)n_roi), Ws((size_t)n_roi), offs((size_t)n_roi + 1);
+    std::vector<int32_t> dl((size_t)n_roi * n_delays);
+    for (int r = 0; r < n_roi; ++r) {
+        Hs[(size_t)r] = h[r];
+        Ws[(size_t)r] = w[r];
+        offs[(size_t)r] = r * n_delays;
+        std::copy(delays, delays + n_delays, dl.begin() + (size_t)r * n_delays);
+    }
+    offs[(size_t)n_roi] = n_roi * n_delays;
+    nfs_batch *b = nullptr;
+    int rc = nfs_batch_create(n_roi, Hs.data(), Ws.data(), offs.data(), dl.data(), n_qbins, &b);
+    if (rc) return rc;
+    b->roi_H = H;
+    b->roi_W = W;
+    b->rois = rois;
+    b->roi_max_words = max_words;
+    if (cudaMalloc(&b->d_rois, sizeof(RoiRect) * rois.size()) != cudaSuccess ||
+        cudaMalloc(&b->d_crop, sizeof(uint16_t) * (size_t)off) != cudaSuccess) {
+        cudaGetLastError();
+        batch_free(b);
+        return NFS_ENOMEM;
+    }
+    if (cudaMemcpy(b->d_rois, rois.data(), sizeof(RoiRect) * rois.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        batch_free(b);
+        return NFS_ECUDA;
+    }
+    *out = b;
+    return NFS_OK;
+}
+
+int nfs_roi_push_device(nfs_batch *b, const uint16_t *d, int n)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    if (b->rois.empty() || n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 3)) return NFS_EINVAL;
+    const size_t HW = (size_t)b->roi_H * b->roi_W;
+    std::vector<const uint16_t *> ptrs(b->rois.size());
+    std::vector<int> counts(b->rois.size());
+    for (long long done = 0; done < n;) {
+        const int nc = (int)std::min<long long>(kRoiGroup, n - done);
+        cudaError_t e = launch_roi_crop(d + (size_t)done * HW, b->roi_H, b->roi_W, nc, b->d_rois,
+                                        (int)b->rois.size(), b->roi_max_words, b->n_sm, b->d_crop, b->stream);
+        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest crop");
+        b->launches++;
+        // the members' kernels read the crop buffer on the batch's stream, before the next crop
+        for (size_t r = 0; r < b->rois.size(); ++r) {
+            ptrs[r] = b->d_crop + b->rois[r].dst;
+            counts[r] = nc;
+        }
+        if ((rc = nfs_batch_push_device(b, ptrs.data(), counts.data()))) return rc;
+        done += nc;
+    }
+    return b->err;
+}
+
+int nfs_roi_push(nfs_batch *b, const uint16_t *host, int n)
+{
+    int rc = batch_enter(b);
+    if (rc) return rc;
+    if (b->rois.empty() || n < 0 || (n > 0 && !host)) return NFS_EINVAL;
+    if (n == 0) return NFS_OK;
+    const size_t HW = (size_t)b->roi_H * b->roi_W;
+    if (!b->d_full && cudaMalloc(&b->d_full, sizeof(uint16_t) * HW * kRoiGroup) != cudaSuccess) {
+        cudaGetLastError();
+        return NFS_ENOMEM;
+    }
+    const bool locked = is_page_locked(host);
+    for (long long done = 0; done < n;) {
+        const int nc = (int)std::min<long long>(kRoiGroup, n - done);
+        // stream-ordered after the previous group's crop, which reads d_full
+        cudaError_t e = cudaMemcpyAsync(b->d_full, host + (size_t)done * HW, sizeof(uint16_t) * HW * nc,
+                                        cudaMemcpyHostToDevice, b->stream);
+        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest upload");
+        if ((rc = nfs_roi_push_device(b, b->d_full, nc))) return rc;
+        done += nc;
+    }
+    // page-locked sources are copied asynchronously: the caller's buffer is free once they are done
+    if (locked) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest upload");
+    }
+    return b->err;
+}
 
 }  // extern "C"
 

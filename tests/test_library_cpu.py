@@ -60,6 +60,45 @@ def test_null_safety_and_status_text(lib):
     assert lib.nfs_create(64, 64, None, 2, 8, ctypes.byref(ctypes.c_void_p())) == P.NFS_EINVAL
 
 
+def _roi_create(lib, H, W, rois, delays=(1, 2, 5), nq=16):
+    y0, x0, h, w = (np.ascontiguousarray(np.array([r[i] for r in rois], np.int32)) for i in range(4))
+    d = np.ascontiguousarray(np.asarray(delays, np.int32))
+    q = np.full(max(len(rois), 1), nq, np.int32)
+    out = ctypes.c_void_p()
+    rc = lib.nfs_roi_create(H, W, len(rois), y0.ctypes.data, x0.ctypes.data, h.ctypes.data, w.ctypes.data,
+                            d.ctypes.data if d.size else None, d.size, q.ctypes.data, ctypes.byref(out))
+    return rc, out
+
+
+@pytest.mark.parametrize("H,W,rois,delays,nq,want", [
+    (128, 128, [(0, 0, 64, 64), (100, 0, 64, 64)], (1, 2), 16, "EINVAL"),   # below the frame
+    (128, 128, [(0, 70, 64, 64)], (1, 2), 16, "EINVAL"),                     # right of the frame
+    (128, 128, [(-2, 0, 64, 64)], (1, 2), 16, "EINVAL"),
+    (128, 128, [(0, 1, 64, 64)], (1, 2), 16, "EINVAL"),                      # odd x0
+    (128, 128, [(0, 0, 64, 63)], (1, 2), 16, "EINVAL"),                      # odd w
+    (128, 127, [(0, 0, 64, 64)], (1, 2), 16, "EINVAL"),                      # odd W
+    (128, 128, [], (1, 2), 16, "EINVAL"),
+    (128, 128, [(0, 0, 64, 64)], (2, 1), 16, "EINVAL"),                      # delays not increasing
+    (128, 128, [(0, 0, 64, 64)], (), 16, "EINVAL"),
+    (128, 128, [(0, 0, 64, 64)], (1, 2), 0, "EINVAL"),
+    (128, 128, [(0, 0, 64, 64), (0, 0, 50, 64)], (1, 2), 16, "EUNSUPPORTED"),  # 50 = 2 x 5 x 5
+    (128, 128, [(0, 0, 10, 64)], (1, 2), 16, "EUNSUPPORTED"),
+])
+def test_roi_create_rejects(lib, H, W, rois, delays, nq, want):
+    rc, out = _roi_create(lib, H, W, rois, delays, nq)
+    assert rc == getattr(P, "NFS_" + want) and not out.value
+
+
+def test_roi_null_safety(lib):
+    assert lib.nfs_roi_push(None, None, 0) == P.NFS_EINVAL
+    assert lib.nfs_roi_push_device(None, None, 0) == P.NFS_EINVAL
+    one = np.zeros(1, np.int32)
+    assert lib.nfs_roi_create(64, 64, 1, None, one.ctypes.data, one.ctypes.data, one.ctypes.data, one.ctypes.data,
+                              1, one.ctypes.data, ctypes.byref(ctypes.c_void_p())) == P.NFS_EINVAL
+    assert lib.nfs_roi_create(64, 64, 1, one.ctypes.data, one.ctypes.data, one.ctypes.data, one.ctypes.data,
+                              one.ctypes.data, 1, one.ctypes.data, None) == P.NFS_EINVAL
+
+
 def test_no_cpu_fallback_in_product_path():
     """The package never imports the oracle: the product path has no CPU route."""
     import paper_1209_3362_gb300
