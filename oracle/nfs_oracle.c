@@ -24,13 +24,15 @@
  *        C_b = sum of w_k over the bin,  D_b(tau_j) = sum_{k in b} w_k D(k, tau_j) / C_b.
  *
  * Readings where the paper is silent: the FFT sign and scale (e^{-i}, unscaled), the DC mode
- * (excluded: its difference is 0 in exact arithmetic), the binning rule above, and mean
- * normalisation rather than division by the zero-frequency value (they differ by a constant).
+ * (excluded: its difference is 0 in exact arithmetic), the binning rule above, mean
+ * normalisation rather than division by the zero-frequency value (they differ by a constant), and
+ * a frame whose spatial mean is 0 (a dark frame) normalising to the zero image.
  *
  * Parity pins (tests/test_oracle.py): the FFT against brute-force DFT sums, Parseval's identity,
  * exact zeros at tau = 0 and for identical frames, time-reversal and intensity-scale invariance,
- * the FFT-linearity route, a travelling-cosine closed form, the Ornstein-Uhlenbeck statistical
- * closed form of Eq. 1, and the bin table against a brute-force count.
+ * the FFT-linearity route, a travelling-cosine closed form (also with dark frames), the
+ * Ornstein-Uhlenbeck statistical closed form of Eq. 1, and the bin table against a brute-force
+ * count.
  */
 #include <math.h>
 #include <stdint.h>
@@ -245,7 +247,8 @@ typedef struct {
     int N, H, W, normalize;
 } frame_src;
 
-/* dst = n_t: frame t divided by its spatial mean (or copied when normalize == 0). */
+/* dst = n_t: frame t divided by its spatial mean (or copied when normalize == 0).  A frame whose
+ * spatial mean is 0 (a dark frame: every uint16 count 0) normalises to the zero image. */
 static void load_frame(const frame_src *s, int t, double *dst)
 {
     size_t n = (size_t)s->H * s->W;
@@ -254,13 +257,14 @@ static void load_frame(const frame_src *s, int t, double *dst)
         uint64_t sum = 0;
         for (size_t i = 0; i < n; ++i) sum += src[i];
         double mean = (double)sum / (double)n;
-        for (size_t i = 0; i < n; ++i) dst[i] = s->normalize ? (double)src[i] / mean : (double)src[i];
+        for (size_t i = 0; i < n; ++i)
+            dst[i] = !s->normalize ? (double)src[i] : (mean != 0.0 ? (double)src[i] / mean : 0.0);
     } else {
         const double *src = s->f64 + (size_t)t * n;
         double sum = 0.0;
         for (size_t i = 0; i < n; ++i) sum += src[i];
         double mean = sum / (double)n;
-        for (size_t i = 0; i < n; ++i) dst[i] = s->normalize ? src[i] / mean : src[i];
+        for (size_t i = 0; i < n; ++i) dst[i] = !s->normalize ? src[i] : (mean != 0.0 ? src[i] / mean : 0.0);
     }
 }
 
@@ -467,7 +471,8 @@ int nfsor_mode_power_u16(const uint16_t *frames, int N, int H, int W, int kx, in
         for (int t = 0; t < npairs; ++t) {
             const uint16_t *fa = frames + (size_t)t * n;
             const uint16_t *fb = frames + (size_t)(t + tau) * n;
-            double ia = 1.0 / mean[t], ib = 1.0 / mean[t + tau];
+            double ia = mean[t] != 0.0 ? 1.0 / mean[t] : 0.0;  /* a dark frame normalises to 0 */
+            double ib = mean[t + tau] != 0.0 ? 1.0 / mean[t + tau] : 0.0;
             double sr = 0.0, si = 0.0;
             for (int y = 0; y < H; ++y) {
                 double rr = 0.0, ri = 0.0;

@@ -171,6 +171,44 @@ def test_travelling_cosine_closed_form(oracle_lib):
     assert list(r["pair_counts"]) == [N - t for t in delays]
 
 
+def test_dark_frames_closed_form(oracle_lib):
+    """Dark frames (spatial mean 0) normalise to the zero image.  With frames c_t (1 + eps cos(2 pi
+    k0.x + omega t)) (any scale c_t > 0) and dark frames in between: a pair of two lit frames gives
+    (eps HW / 2)^2 2 (1 - cos(omega tau)) at k0 and 0 at DC; a pair with one dark frame gives
+    (eps HW / 2)^2 at k0 and (HW)^2 at DC; every other mode 0."""
+    H, W, kx0, ky0, eps, om = 24, 32, 3, 5, 0.2, 0.37
+    N = 12
+    dark = {0, 4, 5}
+    n = S.travelling_cosine_frames(N, H, W, kx0, ky0, eps, om)
+    scale = 1.0 + np.arange(N)
+    frames = n * scale[:, None, None]
+    for t in dark:
+        frames[t] = 0.0
+    delays = [0, 1, 2, 5, 11]
+    r = oracle_lib.structure_function(frames, delays, 16, normalize=True, want_2d=True)
+    amp = (eps * H * W / 2.0) ** 2
+    for j, tau in enumerate(delays):
+        pairs = [(t, t + tau) for t in range(N - tau)]
+        lit = sum(1 for a, b in pairs if a not in dark and b not in dark)
+        one = sum(1 for a, b in pairs if (a in dark) != (b in dark))
+        D2 = r["D2d"][j]
+        exp_k0 = (lit * amp * 2.0 * (1.0 - math.cos(om * tau)) + one * amp) / len(pairs)
+        exp_dc = one * float(H * W) ** 2 / len(pairs)
+        assert abs(D2[ky0, kx0] - exp_k0) <= 1e-12 * amp
+        assert abs(D2[0, 0] - exp_dc) <= 1e-12 * float(H * W) ** 2
+        mask = np.ones_like(D2, bool)
+        mask[ky0, kx0] = False
+        mask[0, 0] = False
+        assert np.max(np.abs(D2[mask])) <= 1e-12 * amp
+    # uint16 frames: the one-mode route agrees with the full oracle when frames are dark
+    u = np.clip(np.rint(frames * 1000.0), 0, 4095).astype(np.uint16)
+    ru = oracle_lib.structure_function(u, [1, 4], 16, want_2d=True)
+    for j, tau in enumerate([1, 4]):
+        for kx, ky in ((kx0, ky0), (0, 1), (W // 2, 7)):
+            v = oracle_lib.mode_power(u, kx, ky, tau)
+            assert abs(v - ru["D2d"][j][ky, kx]) <= 1e-12 * max(abs(v), amp)
+
+
 def test_ou_statistical_closed_form(oracle_lib):
     """Eq. 1 with f = exp(-Gamma tau) and no noise: E D(k, tau) = 2 eps^2 s^2 (HW)^2 S_k (1 - e^{-Gamma_k tau}).
 
