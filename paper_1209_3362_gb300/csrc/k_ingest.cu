@@ -60,26 +60,31 @@ cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g,
     return cudaGetLastError();
 }
 
-// ref[x] = fl32(i_0(x) / <i_0>): the first normalised frame.  Any fixed image would do (it cancels
-// in every difference); this one removes the static beam before the FP32 transform.
-__global__ void k_reference(const uint16_t *__restrict__ frame0, const unsigned long long *__restrict__ sum0,
+// ref[x] = fl32(i_f(x) / <i_f>) for the first frame f < nf whose sum is not 0 (a dark frame
+// normalises to the zero image, which would leave the static beam in every transform); the zero
+// image when all nf frames are dark.  Any fixed image would do (it cancels in every difference);
+// this one removes the static beam before the FP32 transform.
+__global__ void k_reference(const uint16_t *__restrict__ frames, const unsigned long long *__restrict__ sums, int nf,
                             size_t HW, float *__restrict__ ref)
 {
-    unsigned long long S = *sum0;
-    double inv = S ? (double)HW / (double)S : 0.0;
+    int f = 0;
+    while (f < nf && sums[f] == 0) ++f;
+    const unsigned long long S = f < nf ? sums[f] : 0;
+    const double inv = S ? (double)HW / (double)S : 0.0;
+    const uint16_t *frame = frames + (size_t)(f < nf ? f : 0) * HW;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += (size_t)gridDim.x * blockDim.x)
-        ref[i] = (float)((double)frame0[i] * inv);
+        ref[i] = (float)((double)frame[i] * inv);
 }
 
-cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
+cudaError_t launch_reference(const uint16_t *frames, const unsigned long long *sums, int nf, const Geometry &g,
                              float *ref, cudaStream_t s)
 {
+    if (nf <= 0) return cudaErrorInvalidValue;
     int bx = (int)((g.HW + 255) / 256);
     if (bx > 1216) bx = 1216;
-    k_reference<<<bx, 256, 0, s>>>(frame0, sum0, g.HW, ref);
+    k_reference<<<bx, 256, 0, s>>>(frames, sums, nf, g.HW, ref);
     return cudaGetLastError();
 }
-
 
 // Regions of interest: window r of frame f goes to dst + roi[r].dst + f*h*w, row-major (a plain
 // crop; every window is then analysed as a sequence of its own).  One grid row per window, 4-byte

@@ -363,7 +363,8 @@ int flush_block(nfs_ctx *c)
 }
 
 // Exact spatial sums of n device-resident frames (n <= kMaxChunk) into sums[0 .. n), in one launch
-// for a whole copy chunk; the reference image comes from the first frame the context ever sees.
+// for a whole copy chunk; the reference image comes from the first group the context ever sees
+// (its first frame that is not dark).
 int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums)
 {
     CK(c, cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * (size_t)n, c->stream));
@@ -371,7 +372,7 @@ int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums
                    "frame_sums");
     if (rc) return rc;
     if (!c->have_ref && c->f32()) {
-        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, sums, c->g, c->d_ref, c->stream); },
+        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, sums, n, c->g, c->d_ref, c->stream); },
                    "reference");
         if (rc) return rc;
         c->have_ref = true;

@@ -65,8 +65,9 @@ Geometry make_geometry(int H, int W, bool colmajor);
 cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
                               cudaStream_t s);
 
-// ref[x] = fl32(i_0(x) / <i_0>): the FP32 normalised first frame.
-cudaError_t launch_reference(const uint16_t *frame0, const unsigned long long *sum0, const Geometry &g,
+// ref[x] = fl32(i_f(x) / <i_f>): the FP32 normalised first frame f < nf whose sum is not 0 (zero
+// if all nf frames are dark).
+cudaError_t launch_reference(const uint16_t *frames, const unsigned long long *sums, int nf, const Geometry &g,
                              float *ref, cudaStream_t s);
 
 // Row pass: for nf frames, normalise (and subtract ref when T = float) and transform every row.

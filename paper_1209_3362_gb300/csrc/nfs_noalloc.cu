@@ -230,7 +230,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
         const uint16_t *src = dev_frames + (size_t)done * g.HW;
         NA_CK(cudaMemsetAsync(sums, 0, sizeof(unsigned long long) * (size_t)nf, s));
         NA_CK(launch_frame_sums(src, nf, g, sums, s));
-        if (done == 0) NA_CK(launch_reference(src, sums, g, ref, s));
+        if (done == 0) NA_CK(launch_reference(src, sums, nf, g, ref, s));
         const int slot0 = (int)(done % R);
         NA_CK(launch_row_fft<float>(src, nf, sums, ref, g, prow, twr, twp, ring, R, slot0, s, scr, nullptr));
         NA_CK(launch_col_fft<float>(nf, g, pcol, twc, ring, R, slot0, s, scr, nullptr));

@@ -284,6 +284,60 @@ def test_full_size_2048_sampled_modes(oracle_lib):
     assert np.all(got["D"] >= 0.0)
 
 
+@pytest.mark.parametrize("path", ["f32", "f64"])
+def test_dark_frames(oracle_lib, path):
+    """Dark frames (every count 0) normalise to the zero image: dark frames at the start (the
+    reference image then comes from the first lit frame) and in the middle of the sequence."""
+    H, W, N, nq = 96, 128, 300, 48
+    fr = S.OUFrameSource(H, W, 0.7, seed=77).frames_numpy(N).copy()
+    fr[[0, 1, 2, 50, 51, 199]] = 0
+    delays = [1, 2, 3, 48, 49, 150, 197]
+    ref = oracle_lib.structure_function(fr, delays, nq)
+    with P.NFS(H, W, delays, nq, path=path) as ctx:
+        ctx.push_frames(fr)
+        got = ctx.structure_function()
+    np.testing.assert_array_equal(got["bin_counts"], ref["bin_counts"])
+    np.testing.assert_array_equal(got["pair_counts"], ref["pair_counts"])
+    assert np.all(np.isfinite(got["D"]))
+    assert rel_err(got, ref) <= (TOL_F32 if path == "f32" else TOL_F64)
+
+
+@pytest.mark.parametrize("H,W,path", [(4096, 4096, "f32"), (4096, 3072, "f32"), (4096, 4096, "f64")])
+def test_max_frame_size(oracle_lib, H, W, path):
+    """The largest frames the library takes (4096 rows; 4096 = the specialised 2048-point row
+    transform, 3072 = the generic radix-3 row transform; 4096-point generic columns): sampled modes
+    of the exported spectra against the oracle's one-mode definition, a delay with one pair only,
+    and the binned D against an FP64 re-binning of the exported spectra."""
+    nq = min(H, W) // 2
+    N = 24
+    delays = [1, 2, 7, 23]
+    fr = S.OUFrameSource(H, W, 1.5, seed=4096 + W, device="cuda", dtype=torch.float32).frames_numpy(N)
+    with P.NFS(H, W, delays, nq, path=path, block_frames=64 if path == "f32" else 0) as ctx:
+        ctx.push_frames(fr)
+        got = ctx.structure_function()
+        spectra = {j: ctx.export_spectrum(j) for j in range(len(delays))}
+    tol = 1e-4 if path == "f32" else 1e-9
+    samples = [(0, 3, 0), (5, 0, 1), (W // 2, 17, 2), (W // 2 - 648, 3000, 0), (31, H // 2 + 2, 3),
+               (W // 2 - 1, H - 1, 1), (2, 2, 3)]
+    for kx, ky, j in samples:
+        ref = oracle_lib.mode_power(fr, kx, ky, delays[j])
+        v = spectra[j][ky, kx]
+        scale = float(np.mean(spectra[j]))
+        assert abs(v - ref) / (abs(ref) + 1e-3 * scale) <= tol, (kx, ky, delays[j], v, ref)
+    b_of, counts, _ = oracle_lib.bins(H, W, nq)
+    np.testing.assert_array_equal(got["bin_counts"], counts)
+    w = np.full((H, W // 2 + 1), 2.0)
+    w[:, 0] = 1.0
+    w[:, W // 2] = 1.0
+    keep = b_of >= 0
+    for j, D2 in spectra.items():
+        sums = np.bincount(b_of[keep], weights=(w * D2)[keep], minlength=nq)
+        Db = np.where(counts > 0, sums / np.maximum(counts, 1), 0.0)
+        np.testing.assert_allclose(got["D"][j], Db, rtol=1e-12, atol=0)
+    assert np.all(got["pair_counts"] == [N - d for d in delays])
+    assert np.all(got["D"][:, counts > 0] > 0.0)
+
+
 @pytest.mark.parametrize("Rmax", [2200, 1700])
 def test_out_of_core_bands_match_in_core(oracle_lib, Rmax):
     """Out-of-core bands (each a pass over host frames with at most Rmax spectra on the device:
