@@ -190,9 +190,7 @@ static_assert(kWarps * 2 * kTw == kDelayBlock, "block = warps x half-warps x fra
 static_assert(kTile == 16, "a half-warp covers one tile: lane = mode + 16 x half");
 
 constexpr int kRedBufs = 3;                      // partial-sum buffers: the writer may lag two batches
-constexpr int kRedStride = kWarps * 32 + 2;      // words per delay slot of a buffer (the +2 puts the
-                                                 // writer's two half-warps, 8 slots apart, on
-                                                 // different banks)
+constexpr int kRedStride = kWarps * 32;          // words per delay slot of a buffer
 
 struct TiledSmem {
     float2 buf[kSlotBuf][kTile];            // slot ring: frame s at row s mod kSlotBuf (128-byte rows)
@@ -318,6 +316,12 @@ __device__ __forceinline__ pk_t psq_acc(pk_t d, pk_t acc)  // acc + {d.re^2, d.i
     asm("fma.rn.f32x2 %0, %1, %1, %2;" : "=l"(r) : "l"(d), "l"(acc));
     return r;
 }
+__device__ __forceinline__ pk_t padd(pk_t a, pk_t b)
+{
+    pk_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
 __device__ __forceinline__ float phsum(pk_t a)
 {
     float lo, hi;
@@ -338,12 +342,17 @@ __device__ __forceinline__ float2 unpk(pk_t a)
     return v;
 }
 
+// Where a consumer lane leaves its partial sum in a batch row: the two half-warps' values of one
+// mode side by side, so the writer reads both with one 8-byte load.
+__device__ __forceinline__ int red_slot(int warp, int lane) { return warp * 32 + 2 * (lane & (kTile - 1)) + (lane >> 4); }
+
 template <bool MASKED, bool WRAP, bool PACKED>
 __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int lane, int warp, int base, int len,
                                        float (*red)[kRedStride], int pend, int hi_lim)
 {
     const float2 *col = &S.buf[0][lane & (kTile - 1)];
     const float2 *p0 = col + (size_t)((base & (kSlotBuf - 1)) * kTile);
+    const int ri = red_slot(warp, lane);
     auto ldf = [&](int off) -> pk_t {  // the value of frame base + off
         const float2 *a = WRAP ? col + (size_t)(((base + off) & (kSlotBuf - 1)) * kTile) : p0 + off * kTile;
         return *reinterpret_cast<const pk_t *>(a);
@@ -365,7 +374,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                 }
                 a[i & 3] = psq_acc(d, a[i & 3]);
             }
-            red[pend + uu][warp * 32 + lane] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
+            red[pend + uu][ri] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
         } else {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -380,7 +389,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                 a[i & 3] = fmaf(dr, dr, a[i & 3]);
                 a[i & 3] = fmaf(di, di, a[i & 3]);
             }
-            red[pend + uu][warp * 32 + lane] = (a[0] + a[1]) + (a[2] + a[3]);
+            red[pend + uu][ri] = (a[0] + a[1]) + (a[2] + a[3]);
         }
         if (uu + 1 < len) w[(kTw - 1 - uu) & (kTw - 1)] = ldf(-uu - 1);
     }
@@ -396,7 +405,7 @@ __device__ __forceinline__ void subrun_dispatch(TiledSmem &S, const pk_t (&xt)[k
 {
     const int base = ta - d0, basew = taw - d0;
     if (hi_lim_w <= 0 || basew + 2 * kTw - 1 < 0) {  // no pair of this warp is valid
-        for (int u = 0; u < len; ++u) red[pend + u][warp * 32 + lane] = 0.f;
+        for (int u = 0; u < len; ++u) red[pend + u][red_slot(warp, lane)] = 0.f;
         return;
     }
     if (basew - (len - 1) >= 0 && hi_lim_w >= 2 * kTw) {
@@ -535,11 +544,14 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (jh + q < n && (unsigned)(jb + jh + q) < (unsigned)nd) {
-                    const float *row = S.red[b][jh + q];
-                    float sum = 0.f;
+                    const pk_t *row = reinterpret_cast<const pk_t *>(S.red[b][jh + q]) + m;
+                    pk_t s0 = 0ull, s1 = 0ull;  // {half 0, half 1} sums over even and odd warps
 #pragma unroll
-                    for (int w = 0; w < kWarps; ++w) sum += row[w * 32 + m] + row[w * 32 + m + kTile];
-                    base[(size_t)(jb + jh + q) * M] = kahan_add(old[q], sum);
+                    for (int w = 0; w < kWarps; w += 2) {
+                        s0 = padd(s0, row[w * 16]);
+                        s1 = padd(s1, row[w * 16 + 16]);
+                    }
+                    base[(size_t)(jb + jh + q) * M] = kahan_add(old[q], phsum(padd(s0, s1)));
                 }
             }
             __syncwarp();
