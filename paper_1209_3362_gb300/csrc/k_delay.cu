@@ -364,7 +364,7 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
     for (int uu = 0; uu < 16; ++uu) {
         if (uu >= len) break;
         if (PACKED) {
-            pk_t a[4] = {0ull, 0ull, 0ull, 0ull};
+            pk_t a[2] = {0ull, 0ull};
 #pragma unroll
             for (int i = 0; i < kTw; ++i) {
                 pk_t d = psub(xt[i], w[(i - uu) & (kTw - 1)]);
@@ -372,9 +372,9 @@ __device__ __forceinline__ void subrun(TiledSmem &S, const pk_t (&xt)[kTw], int 
                     const bool v = (i - uu >= -base) && (i < hi_lim);
                     d = v ? d : 0ull;
                 }
-                a[i & 3] = psq_acc(d, a[i & 3]);
+                a[i & 1] = psq_acc(d, a[i & 1]);
             }
-            red[pend + uu][ri] = (phsum(a[0]) + phsum(a[1])) + (phsum(a[2]) + phsum(a[3]));
+            red[pend + uu][ri] = phsum(padd(a[0], a[1]));
         } else {
             float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
