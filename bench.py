@@ -191,8 +191,8 @@ def run_reference(args, w):
     import oracle
     oracle.build()
     pairs_per_step = n_s * (n_s - 1) // 2
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        oracle.structure_function(fr[:3], [1, 2], 8, nthreads=cores)
+    for _ in range(max(args.warmup, 0)):  # untimed warm-up steps: the same sample
+        oracle.structure_function(fr, list(range(1, n_s)), 8, nthreads=cores)
     times = []
     for _ in range(args.steps):
         t = time.perf_counter()
@@ -207,7 +207,7 @@ def run_reference(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
-                       "n_qbins": w.n_qbins},
+                       "tau_max": w.delays[-1], "n_qbins": w.n_qbins},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
