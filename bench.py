@@ -355,6 +355,21 @@ def main():
     step()
     stage_ms = {k: v[0] for k, v in ctx.timings().items()}
     ctx.set_option(P.OPT_TIMING, 0)
+    # Algorithmic DRAM bytes of every stage of a pass (frames read once by the sums and once by the
+    # row pass, the row pass's half-spectrum scratch written once and read once by the column pass,
+    # ring spectra written once, the delay update's ring slots and accumulators, the accumulators
+    # read once by the binning; the reference image stays in L2), each stage's rate, and the frames/s
+    # a pass moving only these bytes at the measured HBM peak would reach.
+    scratch = w.H * (((w.W // 2 + 1) + 3) // 4 * 4) * 8
+    stage_bytes = {"mean": w.N * w.H * w.W * 2, "rowfft": w.N * (w.H * w.W * 2 + scratch),
+                   "colfft": w.N * (scratch + M * 8), "delay": alg_bytes, "bin": len(w.delays) * M * 8}
+    stage_gbs = {k: b / (stage_ms[k] / 1e3) / 1e9 for k, b in stage_bytes.items() if stage_ms.get(k)}
+    pass_bytes = sum(stage_bytes.values())
+    hbm_bound = {"bytes_per_step": pass_bytes, "frames_per_s": w.N / (pass_bytes / (hbm_peak * 1e9)),
+                 "peak_gbs": hbm_peak}
+    # the pass's own bound: the delay update at the FP32 peak, every other stage at the HBM peak
+    bound_s = alg_flops / (fp32_peak * 1e12) + (pass_bytes - alg_bytes) / (hbm_peak * 1e9)
+    pass_bound = {"ms_per_step": 1e3 * bound_s, "frames_per_s": w.N / bound_s}
 
     # ---- end to end from pinned host memory
     e2e = None
@@ -425,6 +440,7 @@ def main():
                            f"{ctx_bytes(w, K, M) / 1e9:.1f} GB per rank)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "plain_f64_gpu": plain, "stage_ms_per_step": stage_ms,
+                "stage_gbs": stage_gbs, "hbm_bound": hbm_bound, "pass_bound": pass_bound,
                 "delay_pairs_per_step": pairs}
         print(json.dumps(line), flush=True)
     if dist is not None:
