@@ -113,6 +113,32 @@ def test_running_result_and_reset(oracle_lib):
         assert ctx.frame_count == 60
 
 
+@pytest.mark.parametrize("path", ["f32", "f64"])
+def test_empty_and_single_frame(oracle_lib, path):
+    """No frames, an empty push and a single frame: every D is exactly 0 with pair count N - tau
+    clipped at 0 (tau = 0 has one pair of identical frames); then two more frames match the oracle."""
+    H, W, nq = 64, 64, 16
+    delays = [0, 1, 2]
+    fr = S.OUFrameSource(H, W, 1.0, seed=5).frames_numpy(3)
+    _, counts, _ = oracle_lib.bins(H, W, nq)
+    with P.NFS(H, W, delays, nq, path=path) as ctx:
+        r0 = ctx.structure_function()
+        assert np.all(r0["D"] == 0.0) and list(r0["pair_counts"]) == [0, 0, 0]
+        np.testing.assert_array_equal(r0["bin_counts"], counts)
+        ctx.push_frames(np.empty((0, H, W), np.uint16))
+        ctx.push_frames_device(torch.empty((0, H, W), dtype=torch.int16, device="cuda"))
+        ctx.push_frames(fr[:1])
+        r1 = ctx.structure_function()
+        assert np.all(r1["D"] == 0.0) and list(r1["pair_counts"]) == [1, 0, 0]
+        assert np.all(ctx.export_spectrum(1) == 0.0)
+        ctx.push_frames(fr[1:])
+        r3 = ctx.structure_function()
+    ref = oracle_lib.structure_function(fr, delays, nq)
+    assert list(r3["pair_counts"]) == [3, 2, 1]
+    assert np.all(r3["D"][0] == 0.0)
+    assert rel_err(r3, ref) <= (TOL_F32 if path == "f32" else TOL_F64)
+
+
 @pytest.mark.parametrize("H,W,nq,N,delays", [
     (8, 8, 4, 12, [0, 1, 2, 5, 11, 30]),
     (6, 8, 3, 9, [1, 2, 8]),
