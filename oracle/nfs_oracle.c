@@ -196,11 +196,13 @@ static int64_t gcd64(int64_t a, int64_t b)
     return a;
 }
 
-static uint64_t isqrt_u64(uint64_t v)
+/* floor(sqrt(v)) of a 128-bit integer: 4 n_q^2 r2 exceeds 64 bits for large n_q and lcm(H, W). */
+typedef unsigned __int128 u128;
+static uint64_t isqrt_u128(u128 v)
 {
     uint64_t s = (uint64_t)sqrt((double)v);
-    while (s > 0 && s * s > v) --s;
-    while ((s + 1) * (s + 1) <= v) ++s;
+    while (s > 0 && (u128)s * s > v) --s;
+    while ((u128)(s + 1) * (s + 1) <= v) ++s;
     return s;
 }
 
@@ -222,8 +224,8 @@ int nfsor_bins(int H, int W, int nq, int32_t *bin_of_mode, int64_t *counts, doub
             int64_t m = (int64_t)kx * (L / W);
             int64_t n = kys * (L / H);
             uint64_t r2 = (uint64_t)(m * m + n * n);
-            uint64_t a = 4ull * (uint64_t)nq * (uint64_t)nq * r2;
-            int64_t b = (int64_t)(isqrt_u64(a) / (uint64_t)L);
+            u128 a = (u128)4 * (u128)nq * (u128)nq * (u128)r2;
+            int64_t b = (int64_t)(isqrt_u128(a) / (uint64_t)L);
             int keep = (b < nq) && !(kx == 0 && ky == 0);
             if (bin_of_mode) bin_of_mode[(size_t)ky * Wh + kx] = keep ? (int32_t)b : -1;
             if (!keep) continue;

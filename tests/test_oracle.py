@@ -148,6 +148,28 @@ def test_bin_table_matches_exact_brute_force(oracle_lib, H, W, nq):
     assert c.sum() == int(np.sum((f2 < 0.25) & (f2 > 0)))
 
 
+def test_bin_table_exact_beyond_64_bits(oracle_lib):
+    """4 n_q^2 r2 beyond 64 bits (H = 486, W = 2048: lcm 497,664; n_q = 8000): every bin is the
+    largest b with (b L)^2 <= 4 n_q^2 r2, checked in Python integers."""
+    H, W, nq = 486, 2048, 8000
+    b, c, _ = oracle_lib.bins(H, W, nq)
+    L = H * W // math.gcd(H, W)
+    assert 4 * nq * nq * ((W // 2 * (L // W)) ** 2 + (H // 2 * (L // H)) ** 2) >= 2 ** 64
+    cnt = np.zeros(nq, np.int64)
+    for ky in range(H):
+        kys = ky if ky <= H // 2 else ky - H
+        n = kys * (L // H)
+        for kx in range(W // 2 + 1):
+            m = kx * (L // W)
+            bb = math.isqrt(4 * nq * nq * (m * m + n * n)) // L
+            keep = bb < nq and (kx, ky) != (0, 0)
+            if b[ky, kx] != (bb if keep else -1):
+                raise AssertionError((ky, kx, int(b[ky, kx]), bb))
+            if keep:
+                cnt[bb] += 1 if kx in (0, W // 2) else 2
+    np.testing.assert_array_equal(c, cnt)
+
+
 def test_travelling_cosine_closed_form(oracle_lib):
     """n_t = 1 + eps cos(2 pi k0.x + omega t): |Delta I(k0)|^2 = (eps HW / 2)^2 2 (1 - cos(omega tau))."""
     H, W, kx0, ky0, eps, om = 24, 32, 3, 5, 0.2, 0.37
