@@ -77,6 +77,18 @@ int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins
                   nfs_ctx **out);
 
 /*
+ * The radial bin table of an H x W frame with n_qbins bins (the rule above; Fig. 1e,f's azimuthal
+ * average), computed on the host with no device call.  Caller-owned outputs:
+ *   bin_of_mode  [H][W/2+1] int32, row-major over (k_y, k_x): the bin of each half-plane mode or -1
+ *                (the DC mode and |f| >= 0.5); may be NULL
+ *   bin_counts   [n_qbins] C_b, the weighted mode count of each bin (weights 1 or 2)
+ *   q_mean       [n_qbins] weighted mean of q = 2 pi |f| over the bin (0 if empty); may be NULL
+ * NFS_EINVAL for bin_counts NULL or n_qbins outside 1..65536; NFS_EUNSUPPORTED for a shape
+ * nfs_create rejects.  The bins of every context are exactly this table.
+ */
+int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_counts, double *q_mean);
+
+/*
  * Append n_frames frames from HOST memory, contiguous [n_frames][H][W] uint16, row-major.
  * Counts above 4095 are allowed (no clipping).  The frames are copied to the device before the
  * call returns, so the caller may reuse the buffer at once; the analysis itself runs

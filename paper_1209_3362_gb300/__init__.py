@@ -104,6 +104,7 @@ def load_library(path: Optional[str] = None):
         "nfs_batch_launch_count": (I64, [V]),
         "nfs_batch_last_error": (ctypes.c_char_p, [V]),
         "nfs_roi_create": (I, [I, I, I, V, V, V, V, V, I, V, PP]),
+        "nfs_bin_table": (I, [I, I, I, V, V, V]),
         "nfs_roi_push": (I, [V, V, I]),
         "nfs_roi_push_device": (I, [V, V, I]),
         "nfs_fit_loss_grad": (I, [V, V, I, I, V, V, V, V, V, V, V, V]),
@@ -288,6 +289,19 @@ def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) ->
     if rc != NFS_OK:
         raise NFSError(rc, "nfs_structure_function_noalloc")
     return dict(D=D, bin_counts=bc, pair_counts=pc)
+
+
+def bin_table(H: int, W: int, n_qbins: int) -> dict:
+    """The radial bin table (nfs_bin_table): bin_of_mode [H][W/2+1] (-1 = excluded), bin_counts,
+    q_mean.  Host computation only."""
+    L = load_library()
+    b = np.empty((int(H), int(W) // 2 + 1), np.int32)
+    c = np.empty(int(n_qbins), np.int64)
+    q = np.empty(int(n_qbins), np.float64)
+    rc = L.nfs_bin_table(int(H), int(W), int(n_qbins), _ptr(b), _ptr(c), _ptr(q))
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_bin_table")
+    return dict(bin_of_mode=b, bin_counts=c, q_mean=q)
 
 
 def out_of_core_plan(delays, n_frames: int, max_ring_slots: int) -> dict:

@@ -44,12 +44,17 @@ long long gcd_ll(long long a, long long b)
     return a;
 }
 
-unsigned long long isqrt_ull(unsigned long long v)
+// floor(2 nq sqrt(r2) / L) = the largest b with (b L)^2 <= 4 nq^2 r2, exact in 128-bit integers
+// (4 nq^2 r2 exceeds 64 bits once nq lcm(H, W) passes ~3e9).
+unsigned long long radial_bin(unsigned long long r2, long long nq, long long L)
 {
-    unsigned long long r = (unsigned long long)std::sqrt((double)v);
-    while (r > 0 && r * r > v) --r;
-    while ((r + 1) * (r + 1) <= v) ++r;
-    return r;
+    typedef unsigned __int128 u128;
+    const u128 a = (u128)4 * (u128)nq * (u128)nq * (u128)r2;
+    unsigned long long b = (unsigned long long)(2.0 * (double)nq * std::sqrt((double)r2) / (double)L);
+    auto sq = [L](unsigned long long x) { const u128 y = (u128)x * (u128)L; return y * y; };
+    while (b > 0 && sq(b) > a) --b;
+    while (sq(b + 1) <= a) ++b;
+    return b;
 }
 
 struct TimedPair {
@@ -237,36 +242,52 @@ int upload_stage_twiddles(nfs_ctx *c, int L, float2 **dst)
     return NFS_OK;
 }
 
-// Radial bin of every half-plane mode (integer rule of the header), as a CSR list by bin.
-int build_bins(nfs_ctx *c)
+// Radial bin of every half-plane mode (integer rule of the header): bin_of[ky * (W/2+1) + kx] is the
+// bin or -1 (the DC mode and |f| >= 0.5), counts[b] = C_b (weights 1 or 2), qmean[b] the weighted
+// mean of 2 pi |f| over the bin (0 for an empty bin).  Host arithmetic only.
+void bin_table(int H, int W, int nq, std::vector<int> *bin_of, std::vector<long long> *counts,
+               std::vector<double> *qmean)
 {
-    const int H = c->g.H, W = c->g.W, Wh = c->g.Wh, nq = c->nq;
+    const int Wh = W / 2 + 1;
     const long long L = (long long)H / gcd_ll(H, W) * W;
-    std::vector<std::vector<int>> lists((size_t)nq);
     std::vector<double> qsum((size_t)nq, 0.0);
-    c->counts.assign((size_t)nq, 0);
+    bin_of->assign((size_t)H * Wh, -1);
+    counts->assign((size_t)nq, 0);
     for (int ky = 0; ky < H; ++ky) {
         const long long kys = (ky <= H / 2) ? ky : ky - H;
         for (int kx = 0; kx < Wh; ++kx) {
             if (kx == 0 && ky == 0) continue;
             const long long m = (long long)kx * (L / W), n = kys * (L / H);
             const unsigned long long r2 = (unsigned long long)(m * m + n * n);
-            const unsigned long long b = isqrt_ull(4ull * (unsigned long long)nq * (unsigned long long)nq * r2) /
-                                         (unsigned long long)L;
+            const unsigned long long b = radial_bin(r2, nq, L);
             if (b >= (unsigned long long)nq) continue;
-            const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
-            const long long idx = (long long)c->g.mode(kx, ky);
-            lists[b].push_back((int)((idx << 1) | two));
-            c->counts[b] += two ? 2 : 1;
-            qsum[b] += (two ? 2.0 : 1.0) * 2.0 * M_PI * std::sqrt((double)r2) / (double)L;
+            const int w = (kx != 0 && kx != W / 2) ? 2 : 1;
+            (*bin_of)[(size_t)ky * Wh + kx] = (int)b;
+            (*counts)[b] += w;
+            qsum[b] += (double)w * 2.0 * M_PI * std::sqrt((double)r2) / (double)L;
         }
     }
-    c->qmean.assign((size_t)nq, 0.0);
+    qmean->assign((size_t)nq, 0.0);
+    for (int b = 0; b < nq; ++b)
+        if ((*counts)[b]) (*qmean)[b] = qsum[b] / (double)(*counts)[b];
+}
+
+// The bin table of the context as a CSR list of (mode index << 1 | weight-is-2) by bin, on the device.
+int build_bins(nfs_ctx *c)
+{
+    const int H = c->g.H, W = c->g.W, Wh = c->g.Wh, nq = c->nq;
+    std::vector<int> bin_of;
+    bin_table(H, W, nq, &bin_of, &c->counts, &c->qmean);
+    std::vector<std::vector<int>> lists((size_t)nq);
+    for (int ky = 0; ky < H; ++ky)
+        for (int kx = 0; kx < Wh; ++kx) {
+            const int b = bin_of[(size_t)ky * Wh + kx];
+            if (b < 0) continue;
+            const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
+            lists[b].push_back((int)(((long long)c->g.mode(kx, ky) << 1) | two));
+        }
     std::vector<int> off((size_t)nq + 1, 0), modes;
-    for (int b = 0; b < nq; ++b) {
-        off[b + 1] = off[b] + (int)lists[b].size();
-        if (c->counts[b]) c->qmean[b] = qsum[b] / (double)c->counts[b];
-    }
+    for (int b = 0; b < nq; ++b) off[b + 1] = off[b] + (int)lists[b].size();
     modes.reserve((size_t)off[nq]);
     for (int b = 0; b < nq; ++b) modes.insert(modes.end(), lists[b].begin(), lists[b].end());
     CK(c, cudaMalloc(&c->d_bin_off, sizeof(int) * off.size()));
@@ -647,6 +668,21 @@ int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins
                   nfs_ctx **out)
 {
     return create_impl(H, W, delays, n_delays, n_qbins, path, block_frames, out);
+}
+
+int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_counts, double *q_mean)
+{
+    if (!bin_counts || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
+    if (H < 2 || W < 2 || H > kMaxDim || W > kMaxDim || (H % 2) || (W % 2) || !factors_2_3(H) || !factors_2_3(W / 2))
+        return NFS_EUNSUPPORTED;
+    std::vector<int> bin_of;
+    std::vector<long long> counts;
+    std::vector<double> qmean;
+    bin_table(H, W, n_qbins, &bin_of, &counts, &qmean);
+    if (bin_of_mode) std::copy(bin_of.begin(), bin_of.end(), bin_of_mode);
+    std::copy(counts.begin(), counts.end(), bin_counts);
+    if (q_mean) std::copy(qmean.begin(), qmean.end(), q_mean);
+    return NFS_OK;
 }
 
 int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)

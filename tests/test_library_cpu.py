@@ -60,6 +60,24 @@ def test_null_safety_and_status_text(lib):
     assert lib.nfs_create(64, 64, None, 2, 8, ctypes.byref(ctypes.c_void_p())) == P.NFS_EINVAL
 
 
+@pytest.mark.parametrize("H,W,nq", [(6, 8, 3), (48, 64, 24), (64, 96, 100), (2048, 2048, 1024),
+                                    (4096, 3072, 1536), (486, 2048, 8000), (1458, 2048, 2100)])
+def test_bin_table_equals_oracle(lib, oracle_lib, H, W, nq):
+    """The library's radial bin table (host code of its own) equals the oracle's, bin for bin, also
+    where 4 n_q^2 r2 passes 64 bits (the last two shapes)."""
+    got = P.bin_table(H, W, nq)
+    b, c, q = oracle_lib.bins(H, W, nq)
+    np.testing.assert_array_equal(got["bin_of_mode"], b)
+    np.testing.assert_array_equal(got["bin_counts"], c)
+    np.testing.assert_allclose(got["q_mean"], q, rtol=1e-14, atol=0)
+
+
+def test_bin_table_rejects(lib):
+    assert lib.nfs_bin_table(64, 64, 0, None, np.zeros(1, np.int64).ctypes.data, None) == P.NFS_EINVAL
+    assert lib.nfs_bin_table(64, 64, 8, None, None, None) == P.NFS_EINVAL
+    assert lib.nfs_bin_table(64, 70, 8, None, np.zeros(8, np.int64).ctypes.data, None) == P.NFS_EUNSUPPORTED
+
+
 def _roi_create(lib, H, W, rois, delays=(1, 2, 5), nq=16):
     y0, x0, h, w = (np.ascontiguousarray(np.array([r[i] for r in rois], np.int32)) for i in range(4))
     d = np.ascontiguousarray(np.asarray(delays, np.int32))
