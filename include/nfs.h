@@ -356,6 +356,8 @@ int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *
  *   H, W, delays, n_delays, n_qbins   as for nfs_create (delays and outputs are HOST memory)
  *   stream       cudaStream_t to run on (NULL = the legacy default stream); synchronised on return
  *   D, bin_counts, pair_counts        as for nfs_structure_function
+ * Returns NFS_EUNSUPPORTED, before any GPU work, also when 2 (n_qbins lcm(H, W))^2 >= 1.8e19 (its
+ * device-side bin index works in 64-bit integers; nfs_create has no such limit).
  * Returns NFS_ETOOBIG, before any GPU work, when the sizes need more scratch than the array holds:
  * about 8 (tau_max + 32 + n_delays) H (W/2 + 1) bytes plus small tables (for example 128 x 128
  * frames with tau_max = 50 and 50 delays need about 9 MB).

@@ -169,6 +169,9 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
         if (delays[j] < 0 || delays[j] > 65536 || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
     if (H < 2 || W < 2 || H > 4096 || W > 4096 || (H % 2) || (W % 2) || !factors_2_3_na(H) || !factors_2_3_na(W / 2))
         return NFS_EUNSUPPORTED;
+    // The device bin index evaluates 4 nq^2 r2 (r2 up to lcm(H, W)^2 / 2) in 64-bit integers.
+    const double Lq = (double)n_qbins * (double)((long long)H / gcd_na(H, W) * W);
+    if (2.0 * Lq * Lq >= 1.8e19) return NFS_EUNSUPPORTED;
 
     const Geometry g = make_geometry(H, W, true);
     FftPlan prow, pcol;

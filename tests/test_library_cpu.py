@@ -72,6 +72,16 @@ def test_bin_table_equals_oracle(lib, oracle_lib, H, W, nq):
     np.testing.assert_allclose(got["q_mean"], q, rtol=1e-14, atol=0)
 
 
+def test_noalloc_rejects_bins_beyond_64_bits(lib):
+    """The no-allocation entry point's device bin index is 64-bit: n_q lcm(H, W) too large is
+    refused before any GPU work (486 x 2048 frames, lcm 497,664, with 8000 bins)."""
+    d = np.array([1, 2], np.int32)
+    D = np.zeros((2, 8000)); bc = np.zeros(8000, np.int64); pc = np.zeros(2, np.int64)
+    rc = lib.nfs_structure_function_noalloc(None, 0, 486, 2048, d.ctypes.data, 2, 8000, None, D.ctypes.data,
+                                            bc.ctypes.data, pc.ctypes.data)
+    assert rc == P.NFS_EUNSUPPORTED
+
+
 def test_bin_table_rejects(lib):
     assert lib.nfs_bin_table(64, 64, 0, None, np.zeros(1, np.int64).ctypes.data, None) == P.NFS_EINVAL
     assert lib.nfs_bin_table(64, 64, 8, None, None, None) == P.NFS_EINVAL
