@@ -95,6 +95,8 @@ int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_
  * asynchronously on the context's stream.  Page-locked buffers are copied by DMA directly;
  * pageable ones pass through the context's pinned staging buffers.
  * A frame whose pixels sum to 0 has no mean: its normalised image is taken as 0.
+ * A context takes at most 2^31 - 4096 frames between nfs_create/nfs_reset (frame indices in the
+ * kernels are 32-bit): a push beyond that returns NFS_ESTATE and changes nothing.
  * Returns the status of earlier asynchronous work as well (sticky error).
  */
 int nfs_push_frames(nfs_ctx *ctx, const uint16_t *host_frames, int n_frames);
@@ -352,7 +354,8 @@ int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *
  * takes all of its scratch (spectrum ring, accumulators, twiddles, bin table, sums) from one
  * static device array of NFS_NOALLOC_SCRATCH_BYTES, and calls no cudaMalloc, cudaFree or other
  * allocating routine.
- *   dev_frames   n_frames frames in DEVICE memory, [n_frames][H][W] uint16, 2-byte aligned
+ *   dev_frames   n_frames (at most 2^30) frames in DEVICE memory, [n_frames][H][W] uint16, 2-byte
+ *                aligned
  *   H, W, delays, n_delays, n_qbins   as for nfs_create (delays and outputs are HOST memory)
  *   stream       cudaStream_t to run on (NULL = the legacy default stream); synchronised on return
  *   D, bin_counts, pair_counts        as for nfs_structure_function

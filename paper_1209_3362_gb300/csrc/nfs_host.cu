@@ -24,6 +24,8 @@ constexpr int kDefaultChunkF32 = 32; // FFT chunk of the FP32 path (measured on 
                                      // column passes 19.0 us per frame at 32 frames per launch pair,
                                      // 19.6 at 16, 24.0 at 4)
 constexpr int kMaxDim = 4096;
+// Frames a context takes between resets: the delay kernels index frames with 32-bit integers.
+constexpr long long kMaxFrames = (1LL << 31) - 4096;
 constexpr int kMaxDelay = 65536;
 
 bool factors_2_3(int n)
@@ -691,6 +693,7 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
     if (rc) return rc;
     if (n < 0 || (n > 0 && !h)) return NFS_EINVAL;
     if (n == 0) return NFS_OK;
+    if (c->nframes + n > kMaxFrames) return NFS_ESTATE;
     const bool locked = is_page_locked(h);
     if (!locked && !c->h_stage[0]) {
         for (int i = 0; i < 2; ++i) {
@@ -746,6 +749,7 @@ int nfs_push_frames_device(nfs_ctx *c, const uint16_t *d, int n)
     int rc = enter(c);
     if (rc) return rc;
     if (n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 1)) return NFS_EINVAL;
+    if (c->nframes + n > kMaxFrames) return NFS_ESTATE;
     long long done = 0;
     while (done < n) {
         const int ng = (int)std::min<long long>(kMaxChunk, n - done);
@@ -1531,7 +1535,7 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
                                        int64_t *n_transforms)
 {
     if (!delays || n_delays <= 0 || n_qbins <= 0 || !D || !bin_counts || !pair_counts) return NFS_EINVAL;
-    if (n_frames < 0 || n_frames > 0x7fffffffLL || (n_frames > 0 && !frames)) return NFS_EINVAL;
+    if (n_frames < 0 || n_frames > kMaxFrames || (n_frames > 0 && !frames)) return NFS_EINVAL;
     for (int j = 0; j < n_delays; ++j)
         if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
     std::vector<Band> bands;

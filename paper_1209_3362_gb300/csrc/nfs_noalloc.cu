@@ -162,7 +162,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
                                               const int32_t *delays, int n_delays, int n_qbins, void *stream,
                                               double *D, int64_t *bin_counts, int64_t *pair_counts)
 {
-    if (n_frames < 0 || (n_frames > 0 && !dev_frames) || (reinterpret_cast<uintptr_t>(dev_frames) & 1) || !delays ||
+    if (n_frames < 0 || n_frames > (1 << 30) || (n_frames > 0 && !dev_frames) || (reinterpret_cast<uintptr_t>(dev_frames) & 1) || !delays ||
         n_delays <= 0 || n_delays > 65535 || n_qbins <= 0 || n_qbins > 65536 || !D || !bin_counts || !pair_counts)
         return NFS_EINVAL;
     for (int j = 0; j < n_delays; ++j)

@@ -82,6 +82,20 @@ def test_noalloc_rejects_bins_beyond_64_bits(lib):
     assert rc == P.NFS_EUNSUPPORTED
 
 
+def test_frame_count_limits(lib):
+    """Frame indices in the kernels are 32-bit: the no-allocation entry point and the out-of-core
+    driver refuse frame counts beyond their limits before touching memory or the GPU."""
+    d = np.array([1, 2], np.int32)
+    D = np.zeros((2, 8)); bc = np.zeros(8, np.int64); pc = np.zeros(2, np.int64)
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: the count is refused first
+    assert lib.nfs_structure_function_noalloc(fake, (1 << 30) + 1, 64, 64, d.ctypes.data, 2, 8, None,
+                                              D.ctypes.data, bc.ctypes.data, pc.ctypes.data) == P.NFS_EINVAL
+    nt = ctypes.c_int64()
+    assert lib.nfs_structure_function_out_of_core(64, 64, d.ctypes.data, 2, 8, fake, (1 << 31) - 1, 4096,
+                                                  D.ctypes.data, bc.ctypes.data, pc.ctypes.data, None,
+                                                  ctypes.byref(nt)) == P.NFS_EINVAL
+
+
 def test_bin_table_rejects(lib):
     assert lib.nfs_bin_table(64, 64, 0, None, np.zeros(1, np.int64).ctypes.data, None) == P.NFS_EINVAL
     assert lib.nfs_bin_table(64, 64, 8, None, None, None) == P.NFS_EINVAL
