@@ -75,6 +75,44 @@ def test_schedule_is_safe(cross, i):
     assert _simulate(LISTS[i], cross) >= 1
 
 
+def _random_lists(n, seed):
+    """Seeded delay lists of mixed structure: dense runs, sparse delays with random gaps, clusters
+    of short runs far apart, and log spacing with random ends."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for i in range(n):
+        kind = i % 4
+        if kind == 0:  # runs of random length separated by random gaps
+            d, x = [], int(rng.integers(1, 40))
+            while len(d) < int(rng.integers(5, 250)):
+                d.extend(range(x, x + int(rng.integers(1, 30))))
+                x = d[-1] + 1 + int(rng.integers(1, 200))
+        elif kind == 1:  # isolated delays with random gaps (some shorter than a run of 16)
+            d = list(np.cumsum(rng.integers(1, 120, size=int(rng.integers(2, 150)))))
+        elif kind == 2:  # a few clusters far apart
+            d = sorted({int(c) + j for c in rng.integers(1, 8000, size=6) for j in range(int(rng.integers(1, 20)))})
+        else:  # log spacing with random ends and counts
+            hi = int(rng.integers(50, 4000))
+            d = S.log_delays(1, hi, int(rng.integers(10, min(hi, 220))))
+        out.append([int(v) for v in d if 1 <= v <= 60000])
+    return out
+
+
+@pytest.mark.parametrize("cross", [False, True])
+def test_random_delay_lists_are_safe(cross):
+    """120 seeded delay lists of mixed structure; lists too long for the kernel's schedule (which
+    then runs the one-thread-per-mode kernel) are refused by the export and skipped."""
+    checked = 0
+    for d in _random_lists(120, 20260 + int(cross)):
+        try:
+            sc = P.delay_schedule(d, cross)
+        except P.NFSError:
+            continue
+        assert _simulate(d, cross, sc) >= 1
+        checked += 1
+    assert checked >= 90
+
+
 def test_cross_schedule_with_delay_zero():
     # a shifted pass pairs frame u with the other sequence's frame u: delay 0 is computed
     sc = P.delay_schedule([0, 300, 301, 700], cross=True)
