@@ -199,6 +199,31 @@ def test_out_of_core_plan_all_delays(lib):
         assert paper <= p["n_transforms"] <= 6 * paper
 
 
+def test_out_of_core_plan_random(lib):
+    """Seeded delay lists and slot budgets: every plan the planner returns keeps the band invariants
+    and the exact transform count (_check_plan), and every band's delays have a copy schedule for
+    the fused kernel (ordinary for band 0, shifted for the others)."""
+    K = _block()
+    rng = np.random.Generator(np.random.PCG64(1209))
+    planned = 0
+    for _ in range(60):
+        n = int(rng.integers(2, 300))
+        d = np.cumsum(rng.integers(1, int(rng.choice([2, 8, 60, 400])), size=n))
+        d = [int(x) for x in d if x <= 60000]
+        N = int(d[-1] + rng.integers(1, 3000))
+        Rmax = int(rng.integers(3 * K, 3 * K + 6000))
+        try:
+            p = _check_plan(d, N, Rmax)
+        except P.NFSError:
+            continue
+        first, shift = list(p["band_first"]), list(p["band_shift"])
+        for b, sft in enumerate(shift):
+            sc = P.delay_schedule(d[first[b]:first[b + 1]], cross=sft > 0)
+            assert len(sc["stages"]) >= 1
+        planned += 1
+    assert planned >= 40
+
+
 def test_out_of_core_plan_rejects(lib):
     K = _block()
     with pytest.raises(P.NFSError):
