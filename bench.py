@@ -13,7 +13,12 @@ radial binning, ending with the binned D(q, tau) copied to the host.
             relative difference of its binned D from the fused FP32 path's
   cpu_baseline  the FP64 CPU oracle on a bounded sample of pairs of the same frames, extrapolated
             to the whole job by pair count
+  stage_gbs, hbm_bound, pass_bound  each stage's algorithmic DRAM bytes over its time, and the
+            frames/s of a pass bound by HBM alone or by the delay update's FP32 arithmetic plus
+            the other stages' HBM traffic
 
+--workload ragged48 (48 sequences of uneven shapes, one batch) and --workload roi2048 (2048x2048
+frames cut into 16 regions of interest) time the batch paths with frames resident in HBM.
 --impl reference times the FP64 CPU oracle alone (rank 0 only), each step a bounded sample.
 Multi-GPU: each rank analyses its own independent sequence (replicas, weak scaling), no collective
 on the data path; the timing is the max over ranks.
