@@ -156,7 +156,9 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
 #define NFS_OPT_PATH 5         /* read-only: NFS_PATH_* */
 #define NFS_OPT_FFT_CHUNK 6    /* frames transformed per launch pair (1..32 FP32, 1..64 FP64; default 32
-                                  FP32, 4 FP64; 0 = choose by measurement, FP32 path) */
+                                  FP32, 4 FP64; 0 = choose by measurement, FP32 path, only before the
+                                  first frame: the measurement uses the ring and the reference image,
+                                  so NFS_ESTATE once frames were pushed) */
 #define NFS_OPT_DELAY_VARIANT 7 /* fused delay kernel: 0 = tiled, packed f32x2 math (default);
                                    1 = one thread per mode; 2 = tiled, scalar FP32 math */
 #define NFS_OPT_FFT_GENERIC 8   /* 1 = generic FFT kernels even where size-specialised ones exist */

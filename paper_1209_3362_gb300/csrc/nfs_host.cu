@@ -886,7 +886,11 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             c->timing = (int)v;
             return NFS_OK;
         case NFS_OPT_FFT_CHUNK:
-            if (v == 0 && c->f32()) return autotune_fft_chunk(c);
+            if (v == 0 && c->f32()) {
+                // the measurement transforms zero frames into the ring with a zero reference image
+                if (c->nframes > 0 || c->have_ref) return NFS_ESTATE;
+                return autotune_fft_chunk(c);
+            }
             if (v < 1 || v > (c->f32() ? kMaxChunkF32 : kMaxChunk)) return NFS_EINVAL;
             c->fft_chunk = (int)v;
             return NFS_OK;
