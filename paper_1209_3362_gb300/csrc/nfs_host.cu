@@ -9,32 +9,12 @@
 #include <mutex>
 #include <new>
 
-#include "nfs_internal.cuh"
-#include "roi.cuh"
+#include "nfs_host.cuh"
 
 using namespace nfs;
+using namespace nfs::host;
 
 namespace {
-
-constexpr int kDefaultBlock = kDelayBlock;  // K: frames per fused delay update
-constexpr int kMaxBlock = kDelayBlock;      // largest K the fused kernel takes
-constexpr int kMaxChunk = 64;       // largest FFT chunk (FP64 path)
-constexpr int kMaxChunkF32 = 32;    // largest FFT chunk of the FP32 path (its scratch holds 32 frames)
-constexpr int kDefaultChunkF32 = 32; // FFT chunk of the FP32 path (measured on 2048x2048 frames: row and
-                                     // column passes 19.0 us per frame at 32 frames per launch pair,
-                                     // 19.6 at 16, 24.0 at 4)
-constexpr int kMaxDim = 4096;
-// Frames a context takes between resets: the delay kernels index frames with 32-bit integers.
-constexpr long long kMaxFrames = (1LL << 31) - 4096;
-constexpr int kMaxDelay = 65536;
-
-bool factors_2_3(int n)
-{
-    if (n <= 0) return false;
-    while (n % 2 == 0) n /= 2;
-    while (n % 3 == 0) n /= 3;
-    return n == 1;
-}
 
 long long gcd_ll(long long a, long long b)
 {
@@ -59,83 +39,10 @@ unsigned long long radial_bin(unsigned long long r2, long long nq, long long L)
     return b;
 }
 
-struct TimedPair {
-    int stage;
-    cudaEvent_t a, b;
-};
-
 }  // namespace
 
-struct nfs_ctx {
-    Geometry g{};
-    int path = NFS_PATH_FUSED_F32;
-    int K = kDefaultBlock;
-    int R = 0, nd = 0, nq = 0;
-    int fft_chunk = 4;
-    int stage_frames = 1;
-    int delay_variant = 0;
-    int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
-    int stall_group = -1; // test hook of the bounded-wait path (NFS_OPT_TEST_STALL_GROUP)
-    bool own_streams = true;   // false for members of a batch (the batch owns the streams)
-    bool defer_delay = false;  // members of a batch: the batch runs the delay update of full blocks
-    int device = 0;
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
-    std::vector<int32_t> delays;
-    int tau_max = 0;
-
-    // Host-push staging: a device ring of n_slots copy chunks of copy_frames frames each, so the
-    // copy stream can run up to about two delay blocks ahead of the kernels; pageable sources pass
-    // through two pinned host chunks first.
-    int copy_frames = 1, n_slots = 2;
-    uint16_t *d_stage = nullptr;
-    uint16_t *h_stage[2] = {nullptr, nullptr};
-    std::vector<cudaEvent_t> ev_filled, ev_free;
-    cudaEvent_t ev_hcopied[2] = {nullptr, nullptr};
-    long long stage_i = 0, hstage_i = 0;
-
-    unsigned long long *d_sums = nullptr;
-    float *d_ref = nullptr;
-    void *d_ring = nullptr;
-    void *d_acc = nullptr;
-    int *d_delays = nullptr;
-    void *d_tw_row = nullptr, *d_tw_post = nullptr, *d_tw_col = nullptr;
-    float2 *d_tws_row = nullptr, *d_tws_col = nullptr;  // per-stage twiddles of the specialised FFTs
-    float2 *d_scratch = nullptr;                         // FP32 row-pass output, kMaxChunkF32 frames
-    FftPlan plan_row, plan_col;
-    int *d_bin_off = nullptr, *d_bin_modes = nullptr;
-    long long *d_pairs = nullptr, *d_counts = nullptr;
-    double *d_D = nullptr, *d_export = nullptr;
-    DelaySchedule *sched = nullptr;  // tiled-kernel schedule (host copy, passed by value); NULL if too long
-    int *d_err = nullptr;
-    // Cross pass (one band of the out-of-core mode): pairs (block frame of the "current" sequence,
-    // older frame of the "old" sequence); the current sequence's spectra go to d_ring_cur (K slots),
-    // the old sequence's to d_ring.  Both sequences advance together: frame u of each per step.
-    bool cross = false;
-    void *d_ring_cur = nullptr;
-    long long transforms = 0;  // frames transformed (both sequences of a cross pass)
-
-    std::vector<long long> counts, pairs_h;
-    std::vector<double> qmean;
-    long long nframes = 0, nprocessed = 0;
-    bool have_ref = false;
-
-    int err = NFS_OK;
-    std::string errmsg;
-
-    int timing = 0;  // 1: events around every launch; 2: around delay-update launches only
-    std::vector<TimedPair> pending;
-    std::vector<cudaEvent_t> pool;
-    double stage_ms[NFS_N_STAGES] = {};
-    long long stage_n[NFS_N_STAGES] = {};
-    long long launches = 0;
-
-    bool f32() const { return path == NFS_PATH_FUSED_F32; }
-    size_t csize() const { return f32() ? sizeof(float2) : sizeof(double2); }
-    size_t asize() const { return f32() ? sizeof(float2) : sizeof(double); }
-    size_t frame_bytes() const { return g.HW * sizeof(uint16_t); }
-};
-
-namespace {
+namespace nfs {
+namespace host {
 
 int set_cuda_error(nfs_ctx *c, cudaError_t e, const char *where)
 {
@@ -147,12 +54,6 @@ int set_cuda_error(nfs_ctx *c, cudaError_t e, const char *where)
     return NFS_ECUDA;
 }
 
-#define CK(ctx, call)                                                   \
-    do {                                                                \
-        cudaError_t _e = (call);                                        \
-        if (_e != cudaSuccess) return set_cuda_error((ctx), _e, #call); \
-    } while (0)
-
 cudaEvent_t pool_get(nfs_ctx *c)
 {
     if (!c->pool.empty()) {
@@ -163,28 +64,6 @@ cudaEvent_t pool_get(nfs_ctx *c)
     cudaEvent_t e = nullptr;
     if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
     return e;
-}
-
-// Runs one launcher with optional event timing around it.
-template <class F>
-int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
-{
-    cudaEvent_t a = nullptr, b = nullptr;
-    const bool on = c->timing == 1 || (c->timing == 2 && stage == NFS_STAGE_DELAY);
-    if (on) {
-        a = pool_get(c);
-        b = pool_get(c);
-        if (!a || !b) return set_cuda_error(c, cudaErrorMemoryAllocation, "cudaEventCreate");
-        CK(c, cudaEventRecord(a, s));
-    }
-    cudaError_t e = f();
-    if (e != cudaSuccess) return set_cuda_error(c, e, what);
-    if (on) {
-        CK(c, cudaEventRecord(b, s));
-        c->pending.push_back({stage, a, b});
-    }
-    if (stage != NFS_STAGE_H2D) c->launches++;
-    return NFS_OK;
 }
 
 int harvest(nfs_ctx *c)
@@ -512,7 +391,6 @@ int autotune_fft_chunk(nfs_ctx *c)
     return NFS_OK;
 }
 
-
 // Frames the next chunk may take so that a chunk never spans two delay blocks.
 int next_chunk(const nfs_ctx *c, long long remaining, int cap)
 {
@@ -545,7 +423,7 @@ int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, i
 }
 
 int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
-                bool cross = false)
+                bool cross)
 {
     if (!out) return NFS_EINVAL;
     if (cross && path != NFS_PATH_FUSED_F32) return NFS_EINVAL;
@@ -657,7 +535,8 @@ bool is_page_locked(const void *p)
     return at.type == cudaMemoryTypeHost;
 }
 
-}  // namespace
+}  // namespace host
+}  // namespace nfs
 
 extern "C" {
 
@@ -1002,608 +881,4 @@ int nfs_fit(nfs_ctx *c, const double *D_in, float *A, float *B, float *Gamma, in
     return e == cudaSuccess ? c->err : set_cuda_error(c, e, "nfs_fit");
 }
 
-// ---------------------------------------------------------------- ragged batch
-
-struct nfs_batch {
-    int n = 0, device = 0, n_sm = 0;
-    std::vector<nfs_ctx *> seq;
-    cudaStream_t stream = nullptr, copy_stream = nullptr;
-    DelaySchedule *d_scheds = nullptr;  // one per sequence
-    BatchItem *d_items = nullptr;       // work list of one launch
-    int *d_err = nullptr;
-    std::vector<BatchItem> items;
-    int err = NFS_OK;
-    std::string errmsg;
-    long long launches = 0;
-    // regions of interest (nfs_roi_create): windows of one H x W camera sequence
-    int roi_H = 0, roi_W = 0;
-    std::vector<RoiRect> rois;
-    RoiRect *d_rois = nullptr;
-    uint16_t *d_crop = nullptr;   // kRoiGroup frames of every window
-    uint16_t *d_full = nullptr;   // kRoiGroup full frames (host pushes), allocated on first use
-    long long roi_max_words = 0;  // 4-byte words of the largest window's group
-};
-
-static void batch_free(nfs_batch *b)
-{
-    if (!b) return;
-    cudaSetDevice(b->device);
-    if (b->stream) cudaStreamSynchronize(b->stream);
-    if (b->copy_stream) cudaStreamSynchronize(b->copy_stream);
-    for (nfs_ctx *c : b->seq) nfs_destroy(c);
-    cudaFree(b->d_scheds);
-    cudaFree(b->d_items);
-    cudaFree(b->d_err);
-    cudaFree(b->d_rois);
-    cudaFree(b->d_crop);
-    cudaFree(b->d_full);
-    if (b->stream) cudaStreamDestroy(b->stream);
-    if (b->copy_stream) cudaStreamDestroy(b->copy_stream);
-    delete b;
-}
-
-static int batch_fail(nfs_batch *b, cudaError_t e, const char *where)
-{
-    if (e == cudaSuccess) return NFS_OK;
-    b->errmsg = std::string(where) + ": " + cudaGetErrorString(e);
-    if (b->err == NFS_OK) b->err = NFS_ECUDA;
-    return NFS_ECUDA;
-}
-
-// One persistent launch over every member whose pending block is full (all = false) or non-empty
-// (all = true).
-static int batch_flush(nfs_batch *b, bool all)
-{
-    b->items.clear();
-    long long total = 0;
-    for (size_t s = 0; s < b->seq.size(); ++s) {
-        nfs_ctx *c = b->seq[s];
-        const long long pend = c->nframes - c->nprocessed;
-        if (pend <= 0 || (!all && pend < c->K)) continue;
-        int nst = 0, nbatch = 0;
-        truncate_schedule(*c->sched, c->nframes - 1, &nst, &nbatch);
-        if (nst > 0) {
-            BatchItem it;
-            it.ring = (const float2 *)c->d_ring;
-            it.acc = (float2 *)c->d_acc;
-            it.sched = b->d_scheds + s;
-            it.t0 = c->nprocessed;
-            it.first = total;
-            it.M = c->g.M;
-            it.R = c->R;
-            it.nb = (int)pend;
-            it.nd = c->nd;
-            it.nst = nst;
-            it.nbatch = nbatch;
-            b->items.push_back(it);
-            total += (long long)(c->g.M / kTile);
-        }
-        c->nprocessed = c->nframes;
-    }
-    if (b->items.empty()) return NFS_OK;
-    cudaError_t e = cudaMemcpyAsync(b->d_items, b->items.data(), sizeof(BatchItem) * b->items.size(),
-                                    cudaMemcpyHostToDevice, b->stream);
-    if (e == cudaSuccess) e = launch_delay_batched(b->d_items, (int)b->items.size(), total, b->d_err, b->n_sm, b->stream);
-    if (e != cudaSuccess) return batch_fail(b, e, "batched delay update");
-    b->launches++;
-    return NFS_OK;
-}
-
-static int batch_enter(nfs_batch *b)
-{
-    if (!b) return NFS_EINVAL;
-    cudaError_t e = cudaSetDevice(b->device);
-    if (e != cudaSuccess) return batch_fail(b, e, "cudaSetDevice");
-    return b->err;
-}
-
-// the device status of the batched launches (after a synchronisation)
-static int batch_check(nfs_batch *b)
-{
-    int dev_err[kDelayErrWords] = {};
-    cudaError_t e = cudaMemcpyAsync(dev_err, b->d_err, sizeof(dev_err), cudaMemcpyDeviceToHost, b->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return batch_fail(b, e, "batch status");
-    if (dev_err[0]) {
-        char buf[160];
-        snprintf(buf, sizeof(buf), "batched delay kernel: a bounded wait gave up (kind %d, cta %d, warp %d, index %d)",
-                 dev_err[1], dev_err[2], dev_err[3], dev_err[4]);
-        b->errmsg = buf;
-        if (b->err == NFS_OK) b->err = NFS_ETIMEOUT;
-    }
-    return b->err;
-}
-
-int nfs_batch_create(int n_seq, const int *H, const int *W, const int32_t *delay_offsets, const int32_t *delays,
-                     const int *n_qbins, nfs_batch **out)
-{
-    if (!out) return NFS_EINVAL;
-    *out = nullptr;
-    if (n_seq <= 0 || !H || !W || !delay_offsets || !delays || !n_qbins) return NFS_EINVAL;
-    for (int s = 0; s < n_seq; ++s)
-        if (delay_offsets[s + 1] <= delay_offsets[s]) return NFS_EINVAL;
-    nfs_batch *b = new (std::nothrow) nfs_batch();
-    if (!b) return NFS_ENOMEM;
-    cudaGetDevice(&b->device);
-    b->n = n_seq;
-    cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
-        batch_free(b);
-        return NFS_ECUDA;
-    }
-    std::vector<DelaySchedule> scheds((size_t)n_seq);
-    for (int s = 0; s < n_seq; ++s) {
-        nfs_ctx *c = nullptr;
-        const int rc = create_impl(H[s], W[s], delays + delay_offsets[s], delay_offsets[s + 1] - delay_offsets[s],
-                                   n_qbins[s], NFS_PATH_FUSED_F32, 0, &c);
-        if (rc) {
-            batch_free(b);
-            return rc;
-        }
-        b->seq.push_back(c);
-        if (!c->sched) {  // delay list too long for the tiled kernel's schedule
-            batch_free(b);
-            return NFS_EUNSUPPORTED;
-        }
-        cudaStreamSynchronize(c->stream);
-        cudaStreamDestroy(c->stream);
-        cudaStreamDestroy(c->copy_stream);
-        c->stream = b->stream;
-        c->copy_stream = b->copy_stream;
-        c->own_streams = false;
-        c->defer_delay = true;
-        scheds[s] = *c->sched;
-        if (autotune_fft_chunk(c)) {
-            batch_free(b);
-            return NFS_ECUDA;
-        }
-    }
-    if (cudaMalloc(&b->d_scheds, sizeof(DelaySchedule) * (size_t)n_seq) != cudaSuccess ||
-        cudaMalloc(&b->d_items, sizeof(BatchItem) * (size_t)n_seq) != cudaSuccess ||
-        cudaMalloc(&b->d_err, sizeof(int) * kDelayErrWords) != cudaSuccess) {
-        cudaGetLastError();
-        batch_free(b);
-        return NFS_ENOMEM;
-    }
-    if (cudaMemcpy(b->d_scheds, scheds.data(), sizeof(DelaySchedule) * (size_t)n_seq, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemset(b->d_err, 0, sizeof(int) * kDelayErrWords) != cudaSuccess) {
-        batch_free(b);
-        return NFS_ECUDA;
-    }
-    *out = b;
-    return NFS_OK;
-}
-
-void nfs_batch_destroy(nfs_batch *b) { batch_free(b); }
-
-int nfs_batch_push(nfs_batch *b, int seq, const uint16_t *host_frames, int n)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    if (seq < 0 || seq >= b->n || n < 0 || (n > 0 && !host_frames)) return NFS_EINVAL;
-    nfs_ctx *c = b->seq[seq];
-    long long done = 0;
-    while (done < n) {
-        const long long room = c->K - (c->nframes - c->nprocessed);
-        if (room <= 0) {
-            if ((rc = batch_flush(b, false))) return rc;
-            continue;
-        }
-        const int m = (int)std::min<long long>(room, n - done);
-        if ((rc = nfs_push_frames(c, host_frames + (size_t)done * c->g.HW, m))) return rc;
-        done += m;
-    }
-    return b->err;
-}
-
-int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const int *n_frames)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    if (!dev_frames || !n_frames) return NFS_EINVAL;
-    std::vector<long long> done((size_t)b->n, 0);
-    for (int s = 0; s < b->n; ++s)
-        if (n_frames[s] < 0 || (n_frames[s] > 0 && !dev_frames[s])) return NFS_EINVAL;
-    for (;;) {
-        bool left = false;
-        for (int s = 0; s < b->n; ++s) {
-            nfs_ctx *c = b->seq[s];
-            const long long rem = n_frames[s] - done[s];
-            if (rem <= 0) continue;
-            left = true;
-            const long long room = c->K - (c->nframes - c->nprocessed);
-            if (room <= 0) continue;
-            const int m = (int)std::min(room, rem);
-            if ((rc = nfs_push_frames_device(c, dev_frames[s] + (size_t)done[s] * c->g.HW, m))) return rc;
-            done[s] += m;
-        }
-        if (!left) break;
-        // every member that still has frames now holds a full block: one launch for all of them
-        if ((rc = batch_flush(b, false))) return rc;
-    }
-    return b->err;
-}
-
-int nfs_batch_structure_function(nfs_batch *b, int seq, double *D, int64_t *bin_counts, int64_t *pair_counts,
-                                 double *q_mean)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    if (seq < 0 || seq >= b->n) return NFS_EINVAL;
-    if ((rc = batch_flush(b, true))) return rc;
-    if ((rc = batch_check(b))) return rc;
-    return nfs_structure_function(b->seq[seq], D, bin_counts, pair_counts, q_mean);
-}
-
-int nfs_batch_reset(nfs_batch *b)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    for (nfs_ctx *c : b->seq)
-        if ((rc = nfs_reset(c))) return rc;
-    return NFS_OK;
-}
-
-int nfs_batch_synchronize(nfs_batch *b)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    return batch_check(b);
-}
-
-nfs_ctx *nfs_batch_member(nfs_batch *b, int seq) { return (b && seq >= 0 && seq < b->n) ? b->seq[seq] : nullptr; }
-
-void *nfs_batch_get_stream(const nfs_batch *b) { return b ? (void *)b->stream : nullptr; }
-
-int64_t nfs_batch_launch_count(const nfs_batch *b)
-{
-    if (!b) return -1;
-    long long n = b->launches;
-    for (nfs_ctx *c : b->seq) n += c->launches;
-    return n;
-}
-
-const char *nfs_batch_last_error(const nfs_batch *b) { return b ? b->errmsg.c_str() : ""; }
-
-// ---------------------------------------------------------------- regions of interest
-
-// Frames cropped per launch: kRoiGroup frames of every window are cut from the full frames in one
-// launch and pushed to the members as one device push.
-constexpr int kRoiGroup = 64;
-
-int nfs_roi_create(int H, int W, int n_roi, const int *y0, const int *x0, const int *h, const int *w,
-                   const int32_t *delays, int n_delays, const int *n_qbins, nfs_batch **out)
-{
-    if (!out) return NFS_EINVAL;
-    *out = nullptr;
-    if (H <= 0 || W <= 0 || (W & 1) || n_roi <= 0 || !y0 || !x0 || !h || !w || !delays || n_delays <= 0 ||
-        !n_qbins)
-        return NFS_EINVAL;
-    std::vector<RoiRect> rois((size_t)n_roi);
-    long long off = 0, max_words = 0;
-    for (int r = 0; r < n_roi; ++r) {
-        if (y0[r] < 0 || x0[r] < 0 || h[r] <= 0 || w[r] <= 0 || (x0[r] & 1) || (w[r] & 1) || y0[r] > H - h[r] ||
-            x0[r] > W - w[r])
-            return NFS_EINVAL;
-        const long long words = (long long)kRoiGroup * h[r] * (w[r] / 2);
-        if (words >= (1LL << 31)) return NFS_EINVAL;  // the crop kernel's 32-bit indices
-        const int rc_args = check_args(h[r], w[r], delays, n_delays, n_qbins[r], NFS_PATH_FUSED_F32, 0);
-        if (rc_args) return rc_args;
-        rois[(size_t)r] = RoiRect{y0[r], x0[r], h[r], w[r], off};
-        off += (2 * words + 127) / 128 * 128;  // each window's frames start 256-byte aligned
-        max_words = std::max(max_words, words);
-    }
-    std::vector<int> Hs((size_t)n_roi), Ws((size_t)n_roi), offs((size_t)n_roi + 1);
-    std::vector<int32_t> dl((size_t)n_roi * n_delays);
-    for (int r = 0; r < n_roi; ++r) {
-        Hs[(size_t)r] = h[r];
-        Ws[(size_t)r] = w[r];
-        offs[(size_t)r] = r * n_delays;
-        std::copy(delays, delays + n_delays, dl.begin() + (size_t)r * n_delays);
-    }
-    offs[(size_t)n_roi] = n_roi * n_delays;
-    nfs_batch *b = nullptr;
-    int rc = nfs_batch_create(n_roi, Hs.data(), Ws.data(), offs.data(), dl.data(), n_qbins, &b);
-    if (rc) return rc;
-    b->roi_H = H;
-    b->roi_W = W;
-    b->rois = rois;
-    b->roi_max_words = max_words;
-    if (cudaMalloc(&b->d_rois, sizeof(RoiRect) * rois.size()) != cudaSuccess ||
-        cudaMalloc(&b->d_crop, sizeof(uint16_t) * (size_t)off) != cudaSuccess) {
-        cudaGetLastError();
-        batch_free(b);
-        return NFS_ENOMEM;
-    }
-    if (cudaMemcpy(b->d_rois, rois.data(), sizeof(RoiRect) * rois.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
-        batch_free(b);
-        return NFS_ECUDA;
-    }
-    *out = b;
-    return NFS_OK;
-}
-
-int nfs_roi_push_device(nfs_batch *b, const uint16_t *d, int n)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    if (b->rois.empty() || n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 3)) return NFS_EINVAL;
-    const size_t HW = (size_t)b->roi_H * b->roi_W;
-    std::vector<const uint16_t *> ptrs(b->rois.size());
-    std::vector<int> counts(b->rois.size());
-    for (long long done = 0; done < n;) {
-        const int nc = (int)std::min<long long>(kRoiGroup, n - done);
-        cudaError_t e = launch_roi_crop(d + (size_t)done * HW, b->roi_H, b->roi_W, nc, b->d_rois,
-                                        (int)b->rois.size(), b->roi_max_words, b->n_sm, b->d_crop, b->stream);
-        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest crop");
-        b->launches++;
-        // the members' kernels read the crop buffer on the batch's stream, before the next crop
-        for (size_t r = 0; r < b->rois.size(); ++r) {
-            ptrs[r] = b->d_crop + b->rois[r].dst;
-            counts[r] = nc;
-        }
-        if ((rc = nfs_batch_push_device(b, ptrs.data(), counts.data()))) return rc;
-        done += nc;
-    }
-    return b->err;
-}
-
-int nfs_roi_push(nfs_batch *b, const uint16_t *host, int n)
-{
-    int rc = batch_enter(b);
-    if (rc) return rc;
-    if (b->rois.empty() || n < 0 || (n > 0 && !host)) return NFS_EINVAL;
-    if (n == 0) return NFS_OK;
-    const size_t HW = (size_t)b->roi_H * b->roi_W;
-    if (!b->d_full && cudaMalloc(&b->d_full, sizeof(uint16_t) * HW * kRoiGroup) != cudaSuccess) {
-        cudaGetLastError();
-        return NFS_ENOMEM;
-    }
-    const bool locked = is_page_locked(host);
-    for (long long done = 0; done < n;) {
-        const int nc = (int)std::min<long long>(kRoiGroup, n - done);
-        // stream-ordered after the previous group's crop, which reads d_full
-        cudaError_t e = cudaMemcpyAsync(b->d_full, host + (size_t)done * HW, sizeof(uint16_t) * HW * nc,
-                                        cudaMemcpyHostToDevice, b->stream);
-        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest upload");
-        if ((rc = nfs_roi_push_device(b, b->d_full, nc))) return rc;
-        done += nc;
-    }
-    // page-locked sources are copied asynchronously: the caller's buffer is free once they are done
-    if (locked) {
-        cudaError_t e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest upload");
-    }
-    return b->err;
-}
-
 }  // extern "C"
-
-// ------------------------------------------------------------------ out-of-core bands
-//
-// When the ring for every delay does not fit, the delays are split into bands processed one after
-// the other, each re-reading the frames from host memory (the paper's FIFO re-upload, organised
-// by delay bands).  Band 0 is an ordinary pass over the delays d with d + K <= the slot budget.
-// A later band with smallest delay lo takes the shift s = floor(lo / K) K and runs a cross pass:
-// current sequence C_u = frame u + s (K-slot ring), old sequence O_u = frame u (ring of
-// e_max + K slots), delays e = d - s, so the pair (C_u, O_{u-e}) is the pair (u + s, u + s - d).
-// The block boundaries of C fall on multiples of K in the original frame index (s is a multiple
-// of K), so every pair is added in the same block and warp as in one in-core pass.
-
-namespace {
-
-// One band: delays [first, last) of the list, shift s (s = 0: the ordinary pass).
-struct Band {
-    int first, last;
-    long long shift;
-};
-
-// Does the tiled kernel's schedule of these (shifted) delays fit its parameter space?
-bool schedule_fits(const std::vector<int> &d, bool cross)
-{
-    std::vector<SubRun> srs;
-    std::vector<Stage> sts;
-    if (!build_delay_schedule(d.data(), (int)d.size(), cross, &srs, &sts)) return false;
-    return srs.size() <= (size_t)kMaxSubRuns && sts.size() <= (size_t)kMaxSchedStages;
-}
-
-int plan_bands(const int32_t *delays, int nd, long long N, long long max_slots, std::vector<Band> *bands,
-               long long *n_transforms)
-{
-    bands->clear();
-    *n_transforms = 0;
-    const long long K = kDefaultBlock;
-    int j = 0;
-    while (j < nd) {
-        const long long lo = delays[j];
-        const bool first = bands->empty();
-        // band 0 runs in place when its first delay fits; later bands are cross passes
-        const bool in_place = first && lo + K <= max_slots;
-        const long long s = in_place ? 0 : lo / K * K;
-        const long long hi_max = in_place ? max_slots - K : max_slots - 2 * K + s;
-        // a cross pass needs its first delay within the budget (always so for budgets of 3K slots)
-        if (!in_place && (lo < K || lo > hi_max)) return NFS_EINVAL;
-        int e = j;
-        while (e < nd && delays[e] <= hi_max) ++e;
-        // keep the band within the tiled kernel's schedule limits
-        for (;;) {
-            std::vector<int> d;
-            for (int q = j; q < e; ++q) d.push_back((int)(delays[q] - s));
-            if (schedule_fits(d, !in_place)) break;
-            e = j + (e - j) / 2;
-            if (e == j) return NFS_EUNSUPPORTED;
-        }
-        bands->push_back({j, e, s});
-        if (in_place)
-            *n_transforms += N;
-        else if (N > s)
-            *n_transforms += 2 * (N - s);
-        j = e;
-    }
-    return NFS_OK;
-}
-
-// A cross pass over host frames: old sequence `old` and current sequence `cur`, n frames each
-// (pinned or pageable; read before the call returns).
-int cross_push(nfs_ctx *c, const uint16_t *cur, const uint16_t *old, long long n)
-{
-    const bool locked = is_page_locked(cur) && is_page_locked(old);
-    if (!locked && !c->h_stage[0]) {
-        for (int i = 0; i < 2; ++i) {
-            cudaError_t e = cudaMallocHost((void **)&c->h_stage[i], c->frame_bytes() * (size_t)c->copy_frames);
-            if (e != cudaSuccess) {
-                cudaGetLastError();
-                return NFS_ENOMEM;
-            }
-        }
-    }
-    // copy nc frames from src into the next staging slot; returns the slot
-    auto stage = [&](const uint16_t *src, int nc, int *slot_out) -> int {
-        const int slot = (int)(c->stage_i++ % c->n_slots);
-        uint16_t *dst = c->d_stage + (size_t)slot * c->copy_frames * c->g.HW;
-        const size_t bytes = c->frame_bytes() * (size_t)nc;
-        CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[slot], 0));
-        int hs = -1;
-        if (!locked) {
-            hs = (int)(c->hstage_i++ & 1);
-            CK(c, cudaEventSynchronize(c->ev_hcopied[hs]));
-            memcpy(c->h_stage[hs], src, bytes);
-            src = c->h_stage[hs];
-        }
-        const int rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
-            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
-        }, "h2d");
-        if (rc) return rc;
-        if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
-        CK(c, cudaEventRecord(c->ev_filled[slot], c->copy_stream));
-        CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[slot], 0));
-        *slot_out = slot;
-        return NFS_OK;
-    };
-    long long done = 0;
-    int last = -1;
-    while (done < n) {
-        const int nc = (int)std::min<long long>(c->copy_frames, n - done);
-        int so = 0, sc = 0, rc;
-        if ((rc = stage(old + (size_t)done * c->g.HW, nc, &so))) return rc;
-        if ((rc = stage(cur + (size_t)done * c->g.HW, nc, &sc))) return rc;
-        const uint16_t *dold = c->d_stage + (size_t)so * c->copy_frames * c->g.HW;
-        const uint16_t *dcur = c->d_stage + (size_t)sc * c->copy_frames * c->g.HW;
-        // the old sequence's first frame (frame 0) gives the reference image
-        if ((rc = frame_sums(c, dold, nc, c->d_sums))) return rc;
-        if ((rc = frame_sums(c, dcur, nc, c->d_sums + kMaxChunk))) return rc;
-        for (int o = 0; o < nc;) {
-            const int nf = next_chunk(c, nc - o, c->fft_chunk);
-            if ((rc = process_chunk(c, dold + (size_t)o * c->g.HW, nf, true, c->d_sums + o))) return rc;
-            if ((rc = process_chunk(c, dcur + (size_t)o * c->g.HW, nf, false, c->d_sums + kMaxChunk + o))) return rc;
-            o += nf;
-        }
-        CK(c, cudaEventRecord(c->ev_free[so], c->stream));
-        CK(c, cudaEventRecord(c->ev_free[sc], c->stream));
-        done += nc;
-        last = sc;
-    }
-    if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_filled[last]));
-    return c->err;
-}
-
-}  // namespace
-
-extern "C" {
-
-int nfs_out_of_core_plan(const int32_t *delays, int n_delays, int64_t n_frames, int64_t max_ring_slots,
-                         int32_t *band_first, int64_t *band_shift, int *n_bands, int64_t *n_transforms)
-{
-    if (!delays || n_delays <= 0 || n_frames < 0 || !n_bands || !n_transforms) return NFS_EINVAL;
-    for (int j = 0; j < n_delays; ++j)
-        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
-    std::vector<Band> bands;
-    long long nt = 0;
-    const int rc = plan_bands(delays, n_delays, n_frames, max_ring_slots, &bands, &nt);
-    if (rc) return rc;
-    *n_bands = (int)bands.size();
-    *n_transforms = nt;
-    for (size_t b = 0; b < bands.size(); ++b) {
-        if (band_first) band_first[b] = bands[b].first;
-        if (band_shift) band_shift[b] = bands[b].shift;
-    }
-    if (band_first) band_first[bands.size()] = n_delays;
-    return NFS_OK;
-}
-
-int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int n_delays, int n_qbins,
-                                       const uint16_t *frames, int64_t n_frames, int64_t max_ring_slots, double *D,
-                                       int64_t *bin_counts, int64_t *pair_counts, double *q_mean,
-                                       int64_t *n_transforms)
-{
-    if (!delays || n_delays <= 0 || n_qbins <= 0 || !D || !bin_counts || !pair_counts) return NFS_EINVAL;
-    if (n_frames < 0 || n_frames > kMaxFrames || (n_frames > 0 && !frames)) return NFS_EINVAL;
-    for (int j = 0; j < n_delays; ++j)
-        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
-    std::vector<Band> bands;
-    long long planned = 0;
-    int rc = plan_bands(delays, n_delays, n_frames, max_ring_slots, &bands, &planned);
-    if (rc) return rc;
-    const size_t HW = (size_t)H * W;
-    long long done = 0;
-    std::vector<double> Db;
-    std::vector<int64_t> pc;
-    for (const Band &b : bands) {
-        const int nb = b.last - b.first;
-        std::vector<int32_t> d(delays + b.first, delays + b.last);
-        for (int32_t &x : d) x -= (int32_t)b.shift;
-        nfs_ctx *c = nullptr;
-        rc = create_impl(H, W, d.data(), nb, n_qbins, NFS_PATH_FUSED_F32, 0, &c, b.shift > 0);
-        if (rc) return rc;
-        Db.assign((size_t)nb * n_qbins, 0.0);
-        pc.assign((size_t)nb, 0);
-        if (b.shift == 0)
-            rc = n_frames > 0 ? nfs_push_frames(c, frames, (int)n_frames) : NFS_OK;
-        else if (n_frames > b.shift)
-            rc = cross_push(c, frames + (size_t)b.shift * HW, frames, n_frames - b.shift);
-        if (!rc) rc = nfs_structure_function(c, Db.data(), bin_counts, pc.data(), q_mean);
-        done += c->transforms;
-        nfs_destroy(c);
-        if (rc) return rc;
-        std::copy(Db.begin(), Db.end(), D + (size_t)b.first * n_qbins);
-        for (int q = 0; q < nb; ++q) pair_counts[b.first + q] = n_frames > b.shift ? pc[q] : 0;
-    }
-    if (done != planned) return NFS_ESTATE;  // the passes transformed other frames than planned
-    if (n_transforms) *n_transforms = done;
-    return NFS_OK;
-}
-
-}  // extern "C"
-
-extern "C" int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *subruns, int32_t *stages,
-                                  int max_entries, int *n_subruns, int *n_stages, int *block_frames,
-                                  int *slot_rows, int *copy_barriers)
-{
-    if (!delays || n_delays <= 0 || !n_subruns || !n_stages) return NFS_EINVAL;
-    for (int j = 0; j < n_delays; ++j)
-        if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
-    std::vector<SubRun> srs;
-    std::vector<Stage> sts;
-    if (!build_delay_schedule(delays, n_delays, cross != 0, &srs, &sts)) return NFS_EUNSUPPORTED;
-    *n_subruns = (int)srs.size();
-    *n_stages = (int)sts.size();
-    if (block_frames) *block_frames = kDelayBlock;
-    if (slot_rows) *slot_rows = kSlotBuf;
-    if (copy_barriers) *copy_barriers = kFullBars;
-    if ((subruns && (int)srs.size() > max_entries) || (stages && (int)sts.size() > max_entries)) return NFS_ETOOBIG;
-    for (size_t i = 0; subruns && i < srs.size(); ++i) {
-        subruns[3 * i] = srs[i].j0;
-        subruns[3 * i + 1] = srs[i].len;
-        subruns[3 * i + 2] = srs[i].d0;
-    }
-    for (size_t i = 0; stages && i < sts.size(); ++i) {
-        stages[5 * i] = sts[i].sr0;
-        stages[5 * i + 1] = sts[i].nsr;
-        stages[5 * i + 2] = sts[i].lo;
-        stages[5 * i + 3] = sts[i].hi;
-        stages[5 * i + 4] = sts[i].need;
-    }
-    return NFS_OK;
-}
