@@ -28,6 +28,31 @@ def test_exports_every_header_symbol(lib):
     assert set(names) <= exported
 
 
+def test_binding_constants_match_the_header():
+    """Every status, path, option, fit-method and stage constant of the binding equals the header's
+    #define of the same name."""
+    import re
+    defs = {}
+    for line in open(P.HEADER):
+        m = re.match(r"#define (NFS_\w+) \(?(-?\d+)(?:ull)?\)?", line)
+        if m:
+            defs[m.group(1)] = int(m.group(2))
+    pairs = {"NFS_OK": P.NFS_OK, "NFS_EINVAL": P.NFS_EINVAL, "NFS_EUNSUPPORTED": P.NFS_EUNSUPPORTED,
+             "NFS_ENOMEM": P.NFS_ENOMEM, "NFS_ECUDA": P.NFS_ECUDA, "NFS_ESTATE": P.NFS_ESTATE,
+             "NFS_ETOOBIG": P.NFS_ETOOBIG, "NFS_ETIMEOUT": P.NFS_ETIMEOUT,
+             "NFS_PATH_FUSED_F32": P.PATH_FUSED_F32, "NFS_PATH_PLAIN_F64": P.PATH_PLAIN_F64,
+             "NFS_FIT_GAUSS_NEWTON": P.FIT_GAUSS_NEWTON, "NFS_FIT_ADAM": P.FIT_ADAM,
+             "NFS_N_STAGES": len(P.STAGES)}
+    for name in ("TIMING", "BLOCK_FRAMES", "RING_SLOTS", "PITCH", "PATH", "FFT_CHUNK", "DELAY_VARIANT",
+                 "FFT_GENERIC", "TEST_STALL_GROUP"):
+        pairs["NFS_OPT_" + name] = getattr(P, "OPT_" + name)
+    for i, st in enumerate(P.STAGES):
+        assert defs["NFS_STAGE_" + st.upper()] == i, st
+    for k, v in pairs.items():
+        assert defs[k] == v, k
+    assert (defs["NFS_NOALLOC_SCRATCH_BYTES"] << 20) == P.NOALLOC_SCRATCH_BYTES
+
+
 def _create(lib, H, W, delays, nq, path=0, block=0):
     h = ctypes.c_void_p()
     d = np.ascontiguousarray(np.asarray(delays, np.int32))
