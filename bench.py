@@ -397,6 +397,19 @@ def main():
         e2e_s = ranks_max((time.perf_counter() - t0) / args.steps)
         e2e = {"value": job_value(world, w.N, 1000.0 * e2e_s), "unit": "frames/s", "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
                "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
+        # the copy engines' rate from this process's page-locked buffer (1 GiB, alone on the GPU):
+        # the end-to-end rate depends on it, and it varies with the box's state
+        probe = host.view(-1)[: 1 << 29]
+        dev = torch.empty_like(probe, device="cuda")
+        dev.copy_(probe, non_blocking=True)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        dev.copy_(probe, non_blocking=True)
+        p1.record()
+        p1.synchronize()
+        e2e["h2d_probe_gbs"] = probe.numel() * 2 / (p0.elapsed_time(p1) / 1e3) / 1e9
+        del dev
     ctx.close()
 
     # ---- the plain unfused FP64 GPU path, one pass on the same frames
