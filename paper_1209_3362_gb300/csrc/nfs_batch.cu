@@ -193,6 +193,7 @@ void nfs_batch_destroy(nfs_batch *b) { batch_free(b); }
 
 int nfs_batch_push(nfs_batch *b, int seq, const uint16_t *host_frames, int n)
 {
+    NvtxRange range("nfs_batch_push");
     int rc = batch_enter(b);
     if (rc) return rc;
     if (seq < 0 || seq >= b->n || n < 0 || (n > 0 && !host_frames)) return NFS_EINVAL;
@@ -213,6 +214,7 @@ int nfs_batch_push(nfs_batch *b, int seq, const uint16_t *host_frames, int n)
 
 int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const int *n_frames)
 {
+    NvtxRange range("nfs_batch_push_device");
     int rc = batch_enter(b);
     if (rc) return rc;
     if (!dev_frames || !n_frames) return NFS_EINVAL;
@@ -242,6 +244,7 @@ int nfs_batch_push_device(nfs_batch *b, const uint16_t *const *dev_frames, const
 int nfs_batch_structure_function(nfs_batch *b, int seq, double *D, int64_t *bin_counts, int64_t *pair_counts,
                                  double *q_mean)
 {
+    NvtxRange range("nfs_batch_structure_function");
     int rc = batch_enter(b);
     if (rc) return rc;
     if (seq < 0 || seq >= b->n) return NFS_EINVAL;
@@ -340,6 +343,7 @@ int nfs_roi_create(int H, int W, int n_roi, const int *y0, const int *x0, const 
 
 int nfs_roi_push_device(nfs_batch *b, const uint16_t *d, int n)
 {
+    NvtxRange range("nfs_roi_push_device");
     int rc = batch_enter(b);
     if (rc) return rc;
     if (b->rois.empty() || n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 3)) return NFS_EINVAL;
@@ -365,6 +369,7 @@ int nfs_roi_push_device(nfs_batch *b, const uint16_t *d, int n)
 
 int nfs_roi_push(nfs_batch *b, const uint16_t *host, int n)
 {
+    NvtxRange range("nfs_roi_push");
     int rc = batch_enter(b);
     if (rc) return rc;
     if (b->rois.empty() || n < 0 || (n > 0 && !host)) return NFS_EINVAL;

@@ -568,6 +568,7 @@ int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_
 
 int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
 {
+    NvtxRange range("nfs_push_frames");
     int rc = enter(c);
     if (rc) return rc;
     if (n < 0 || (n > 0 && !h)) return NFS_EINVAL;
@@ -625,6 +626,7 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
 
 int nfs_push_frames_device(nfs_ctx *c, const uint16_t *d, int n)
 {
+    NvtxRange range("nfs_push_frames_device");
     int rc = enter(c);
     if (rc) return rc;
     if (n < 0 || (n > 0 && !d) || (reinterpret_cast<uintptr_t>(d) & 1)) return NFS_EINVAL;
@@ -646,6 +648,7 @@ int nfs_push_frames_device(nfs_ctx *c, const uint16_t *d, int n)
 
 int nfs_structure_function(nfs_ctx *c, double *D, int64_t *bin_counts, int64_t *pair_counts, double *q_mean)
 {
+    NvtxRange range("nfs_structure_function");
     int rc = enter(c);
     if (rc) return rc;
     if (!D || !bin_counts || !pair_counts) return NFS_EINVAL;
@@ -688,6 +691,7 @@ int nfs_structure_function(nfs_ctx *c, double *D, int64_t *bin_counts, int64_t *
 
 int nfs_export_spectrum(nfs_ctx *c, int j, double *out)
 {
+    NvtxRange range("nfs_export_spectrum");
     int rc = enter(c);
     if (rc) return rc;
     if (!out || j < 0 || j >= c->nd) return NFS_EINVAL;
@@ -832,6 +836,7 @@ int64_t nfs_launch_count(const nfs_ctx *c) { return c ? c->launches : -1; }
 
 int nfs_fit(nfs_ctx *c, const double *D_in, float *A, float *B, float *Gamma, int iters, int method)
 {
+    NvtxRange range("nfs_fit");
     int rc = enter(c);
     if (rc) return rc;
     if (!A || !B || !Gamma || iters < 0 || (method != NFS_FIT_GAUSS_NEWTON && method != NFS_FIT_ADAM)) return NFS_EINVAL;

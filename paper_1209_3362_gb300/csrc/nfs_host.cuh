@@ -5,10 +5,21 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "nfs_internal.cuh"
 
 namespace nfs {
 namespace host {
+
+// A named NVTX range over a scope: the C ABI's entry points appear as ranges in a profiler's
+// timeline (and can filter ncu captures); without a profiler attached the calls do nothing.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kDefaultBlock = kDelayBlock;  // K: frames per fused delay update
 constexpr int kMaxBlock = kDelayBlock;      // largest K the fused kernel takes

@@ -167,6 +167,7 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
                                        int64_t *bin_counts, int64_t *pair_counts, double *q_mean,
                                        int64_t *n_transforms)
 {
+    NvtxRange range("nfs_structure_function_out_of_core");
     if (!delays || n_delays <= 0 || n_qbins <= 0 || !D || !bin_counts || !pair_counts) return NFS_EINVAL;
     if (n_frames < 0 || n_frames > kMaxFrames || (n_frames > 0 && !frames)) return NFS_EINVAL;
     for (int j = 0; j < n_delays; ++j)
