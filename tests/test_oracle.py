@@ -57,6 +57,16 @@ def test_tau_zero_and_identical_frames_are_exact_zero(oracle_lib):
     assert list(r2["pair_counts"]) == [4, 3, 1]
 
 
+def test_dc_mode_of_normalised_differences_vanishes(oracle_lib):
+    """Mean-normalised frames all sum to HW, so the difference's DC coefficient is 0 in exact
+    arithmetic: in FP64 |Delta I(0)| <= 1e-9 HW (the reason the DC mode is left out of the bins)."""
+    H, W = 24, 32
+    fr = S.uniform_frames(12, H, W, seed=77)
+    r = oracle_lib.structure_function(fr, [1, 3, 7], 8, want_2d=True)
+    assert np.all(r["D2d"][:, 0, 0] <= (1e-9 * H * W) ** 2)
+    assert np.all(r["D2d"][:, 0, 1:].max(axis=1) > 1e6 * r["D2d"][:, 0, 0])
+
+
 def test_time_reversal_invariance(oracle_lib):
     fr = S.uniform_frames(9, 16, 12, seed=4)
     a = oracle_lib.structure_function(fr, [1, 2, 5], 6)["D"]
