@@ -39,10 +39,16 @@ __all__ = [
     "log_delays",
     "Workload",
     "WORKLOADS",
+    "RaggedWorkload",
+    "RAGGED_WORKLOADS",
+    "RoiWorkload",
+    "ROI_WORKLOADS",
     "OUFrameSource",
     "uniform_frames",
     "travelling_cosine_frames",
     "beam_sigma",
+    "ragged_shapes",
+    "workload_source",
 ]
 
 
