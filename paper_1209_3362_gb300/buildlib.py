@@ -45,17 +45,27 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    os.makedirs(OUT, exist_ok=True)
+# Host-code sanitizers for a checking build (the host logic: schedules, band plans, bin tables,
+# argument checks); device code is compiled as usual.
+SANITIZE_FLAGS = ["-Xcompiler", "-fsanitize=address,-fsanitize=undefined,-fno-omit-frame-pointer", "-g"]
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, sanitize: bool = False) -> str:
+    """Compile every translation unit and link the library; returns its path.  sanitize=True builds
+    a separate copy with AddressSanitizer and UBSan in the host code (loaded with libasan preloaded)."""
+    out = OUT + ("_sanitize" if sanitize else "")
+    lib = os.path.join(out, os.path.basename(LIB))
+    os.makedirs(out, exist_ok=True)
     cc = nvcc()
     hdrs = _headers()
     jobs = []
     objs = []
+    extra = SANITIZE_FLAGS if sanitize else []
     for src in _sources():
-        obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            cmd = [cc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
+            cmd = [cc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             jobs.append(cmd)
@@ -70,14 +80,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
                 sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
             if r.returncode:
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", *extra[:2]]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
