@@ -21,22 +21,27 @@ _LIB = os.path.join(_HERE, "_build", "libnfs_oracle.so")
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (OpenMP) into oracle/_build/libnfs_oracle.so."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp",
+def build(force: bool = False, sanitize: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP) into oracle/_build/libnfs_oracle.so; sanitize=True builds
+    a separate copy with AddressSanitizer and UBSan (loaded with libasan preloaded)."""
+    out = _LIB.replace(".so", "_sanitize.so") if sanitize else _LIB
+    os.makedirs(os.path.dirname(out), exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + f".{os.getpid()}.tmp"
+        extra = ["-g", "-fsanitize=address,undefined", "-fno-omit-frame-pointer"] if sanitize else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-fopenmp", *extra,
                                "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+        os.replace(tmp, out)
+    return out
 
 
 def lib():
+    """The compiled oracle (NFS_ORACLE_LIB names another build of the same source, e.g. a
+    sanitizer build)."""
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(_LIB)
+        path = os.environ.get("NFS_ORACLE_LIB") or build()
+        L = ctypes.CDLL(path)
         P = ctypes.c_void_p
         i = ctypes.c_int
         L.nfsor_fft2.argtypes = [i, i, P, P, P, P]

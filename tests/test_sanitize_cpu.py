@@ -1,7 +1,8 @@
-"""The library's host logic under AddressSanitizer and UBSan (no GPU): a copy built with
-sanitize=True runs the copy-schedule export, the band planner, the bin table and the argument
-checks of the creating calls on many seeded inputs in a child process with libasan preloaded; any
-out-of-bounds access, use after free or undefined behaviour ends that process with an error."""
+"""The library's host logic and the oracle under AddressSanitizer and UBSan (no GPU): copies built
+with sanitize=True run the copy-schedule export, the band planner, the bin table and the argument
+checks of the creating calls, and the oracle's transforms, bins and structure functions, on seeded
+inputs in child processes with libasan preloaded; any out-of-bounds access, use after free or
+undefined behaviour ends that process with an error."""
 import os
 import shutil
 import subprocess
@@ -80,5 +81,40 @@ def test_host_logic_under_sanitizers(tmp_path):
     script.write_text(f"ROOT = {ROOT!r}\nLIB = {lib!r}\n" + DRIVER)
     env = dict(os.environ, LD_PRELOAD=asan, ASAN_OPTIONS="detect_leaks=0",
                UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1")
+    r = subprocess.run([sys.executable, str(script)], capture_output=True, text=True, env=env, timeout=600)
+    assert r.returncode == 0 and "clean" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
+
+
+ORACLE_DRIVER = r'''
+import sys
+import numpy as np
+sys.path.insert(0, ROOT)
+import oracle
+import nfs_synth as S
+rng = np.random.Generator(np.random.PCG64(5))
+for H, W in [(6, 8), (12, 16), (9, 6), (24, 32)]:
+    a = rng.standard_normal((H, W)) + 1j * rng.standard_normal((H, W))
+    assert np.allclose(oracle.fft2(a), np.fft.fft2(a))
+for H, W, nq in [(6, 8, 3), (486, 2048, 8000), (64, 96, 100)]:
+    oracle.bins(H, W, nq)
+fr = S.uniform_frames(9, 12, 16, seed=3)
+fr[4] = 0  # a dark frame
+oracle.structure_function(fr, [0, 1, 2, 8, 20], 8, want_2d=True)
+oracle.structure_function(fr.astype(np.float64), [1, 3], 6, normalize=False)
+oracle.mode_power(fr, 3, 5, 2)
+print("clean")
+'''
+
+
+def test_oracle_under_sanitizers(tmp_path):
+    asan = _libasan()
+    if asan is None:
+        pytest.skip("gcc's libasan is not available")
+    import oracle
+    lib = oracle.build(sanitize=True)
+    script = tmp_path / "drive_oracle.py"
+    script.write_text(f"ROOT = {ROOT!r}\n" + ORACLE_DRIVER)
+    env = dict(os.environ, LD_PRELOAD=asan, ASAN_OPTIONS="detect_leaks=0", NFS_ORACLE_LIB=lib,
+               UBSAN_OPTIONS="print_stacktrace=1:halt_on_error=1", OMP_NUM_THREADS="2")
     r = subprocess.run([sys.executable, str(script)], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0 and "clean" in r.stdout, r.stdout[-2000:] + r.stderr[-4000:]
