@@ -3,7 +3,6 @@ header declares, and rejects bad arguments before touching the device."""
 import ctypes
 import os
 import subprocess
-import sys
 
 import numpy as np
 import pytest
