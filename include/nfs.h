@@ -237,7 +237,8 @@ const char *nfs_batch_last_error(const nfs_batch *b);
  * frames, bit for bit.
  *
  * nfs_roi_create: NFS_EINVAL for a window outside the frame, an odd W, x0 or w (the crop moves
- * 4-byte words), an empty list, a NULL pointer or a delay list or bin count nfs_create rejects;
+ * 4-byte words), an empty list or more than 65535 windows, a NULL pointer or a delay list or bin
+ * count nfs_create rejects;
  * NFS_EUNSUPPORTED for a window shape nfs_create rejects (all checked before any CUDA call);
  * NFS_ENOMEM.
  * nfs_roi_push: n_frames full frames [n][H][W] from host memory; the buffer may be reused on

@@ -294,8 +294,9 @@ int nfs_roi_create(int H, int W, int n_roi, const int *y0, const int *x0, const 
 {
     if (!out) return NFS_EINVAL;
     *out = nullptr;
-    if (H <= 0 || W <= 0 || (W & 1) || n_roi <= 0 || !y0 || !x0 || !h || !w || !delays || n_delays <= 0 ||
-        !n_qbins)
+    // n_roi bounds the crop launch's grid rows (65535)
+    if (H <= 0 || W <= 0 || (W & 1) || n_roi <= 0 || n_roi > 65535 || !y0 || !x0 || !h || !w || !delays ||
+        n_delays <= 0 || !n_qbins)
         return NFS_EINVAL;
     std::vector<RoiRect> rois((size_t)n_roi);
     long long off = 0, max_words = 0;

@@ -155,6 +155,16 @@ def test_roi_create_rejects(lib, H, W, rois, delays, nq, want):
     assert rc == getattr(P, "NFS_" + want) and not out.value
 
 
+def test_roi_count_limit(lib):
+    n = 65536
+    z = np.zeros(n, np.int32)
+    e = np.full(n, 8, np.int32)
+    d = np.array([1, 2], np.int32)
+    rc = lib.nfs_roi_create(64, 64, n, z.ctypes.data, z.ctypes.data, e.ctypes.data, e.ctypes.data, d.ctypes.data,
+                            2, e.ctypes.data, ctypes.byref(ctypes.c_void_p()))
+    assert rc == P.NFS_EINVAL
+
+
 def test_roi_null_safety(lib):
     assert lib.nfs_roi_push(None, None, 0) == P.NFS_EINVAL
     assert lib.nfs_roi_push_device(None, None, 0) == P.NFS_EINVAL
