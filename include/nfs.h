@@ -59,8 +59,8 @@ typedef struct nfs_ctx nfs_ctx;
  * Create an analysis context (Eq. 1 for a single image sequence).
  *   H, W      frame height and width in pixels: even, 2 <= H, W <= 4096, prime factors 2 and 3
  *             only; otherwise NFS_EUNSUPPORTED.
- *   delays    n_delays frame delays tau_j, strictly increasing, tau_0 >= 0 (tau = 0 is allowed and
- *             gives D = 0 exactly), tau_max <= 65536.  Copied by the call.
+ *   delays    n_delays (1..65535) frame delays tau_j, strictly increasing, tau_0 >= 0 (tau = 0 is
+ *             allowed and gives D = 0 exactly), tau_max <= 65536.  Copied by the call.
  *   n_qbins   number of radial bins, 1..65536; bins span 0 <= |f| < 0.5 cycles/px evenly.
  *   *out      receives the context; NULL on failure.
  * Allocates the spectrum ring (tau_max + K slots of H x (W/2+1) complex values), the

@@ -410,7 +410,8 @@ int enter(nfs_ctx *c)
 // The argument checks of nfs_create_ex, made before any CUDA call.
 int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block)
 {
-    if (!delays || n_delays <= 0 || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
+    // n_delays is the binning launch's grid rows (at most 65535)
+    if (!delays || n_delays <= 0 || n_delays > 65535 || n_qbins <= 0 || n_qbins > 65536) return NFS_EINVAL;
     if (path != NFS_PATH_FUSED_F32 && path != NFS_PATH_PLAIN_F64) return NFS_EINVAL;
     if (block < 0 || block > kMaxBlock) return NFS_EINVAL;
     for (int j = 0; j < n_delays; ++j) {

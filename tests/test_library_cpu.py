@@ -68,7 +68,8 @@ def test_rejects_unsupported_shapes(lib, H, W):
 
 @pytest.mark.parametrize("delays,nq,path,block", [([2, 1], 8, 0, 0), ([1, 1], 8, 0, 0), ([-1, 2], 8, 0, 0),
                                                   ([], 8, 0, 0), ([1, 2], 0, 0, 0), ([1, 2], 8, 7, 0),
-                                                  ([1, 2], 8, 0, 513), ([1, 70000], 8, 0, 0)])
+                                                  ([1, 2], 8, 0, 513), ([1, 70000], 8, 0, 0),
+                                                  (list(range(1, 65537)), 8, 0, 0)])
 def test_rejects_bad_arguments(lib, delays, nq, path, block):
     rc, h = _create(lib, 64, 64, delays, nq, path, block)
     assert rc == P.NFS_EINVAL and not h.value
