@@ -67,6 +67,20 @@ def test_dc_mode_of_normalised_differences_vanishes(oracle_lib):
     assert np.all(r["D2d"][:, 0, 1:].max(axis=1) > 1e6 * r["D2d"][:, 0, 0])
 
 
+def test_transpose_and_flip_invariance(oracle_lib):
+    """Radial bins depend on |f| only, so transposing every frame (H x W -> W x H, which swaps the
+    roles of k_x and k_y and of the half-plane axis) or mirroring it leaves every binned D unchanged;
+    a swapped axis scale or half-plane weight would not."""
+    fr = S.uniform_frames(10, 24, 32, seed=31)
+    delays = [1, 2, 5]
+    ref = oracle_lib.structure_function(fr, delays, 10)
+    for g in (np.ascontiguousarray(fr.transpose(0, 2, 1)), np.ascontiguousarray(fr[:, :, ::-1]),
+              np.ascontiguousarray(fr[:, ::-1, :])):
+        r = oracle_lib.structure_function(g, delays, 10)
+        np.testing.assert_array_equal(r["bin_counts"], ref["bin_counts"])
+        np.testing.assert_allclose(r["D"], ref["D"], rtol=1e-11, atol=0)
+
+
 def test_time_reversal_invariance(oracle_lib):
     fr = S.uniform_frames(9, 16, 12, seed=4)
     a = oracle_lib.structure_function(fr, [1, 2, 5], 6)["D"]
