@@ -94,12 +94,14 @@ static void dft_rec(int len, const cplx *x, int stride, cplx *X, cplx *scratch, 
         for (int s = 0; s < p; ++s) {
             int kk = k + s * m;
             double ar = 0.0, ai = 0.0;
+            long e = 0; /* (r * kk) mod len, advanced by kk per term */
             for (int r = 0; r < p; ++r) {
-                long e = ((long)r * kk) % len;
                 cplx w = tw[e * step];
                 cplx y = X[(size_t)r * m + k];
                 ar += w.re * y.re - w.im * y.im;
                 ai += w.re * y.im + w.im * y.re;
+                e += kk;
+                if (e >= len) e -= len;
             }
             scratch[kk].re = ar;
             scratch[kk].im = ai;
@@ -109,10 +111,12 @@ static void dft_rec(int len, const cplx *x, int stride, cplx *X, cplx *scratch, 
 }
 
 /* Workspace for 2-D transforms of one H x W shape. */
+#define COLS_PER_GATHER 8 /* columns copied out together (whole cache lines per row) */
 typedef struct {
     int H, W;
     cplx *twH, *twW;
     cplx *line_in, *line_out, *scratch;
+    cplx *cols; /* COLS_PER_GATHER columns of H values each */
 } fft2_plan;
 
 static void fft2_free(fft2_plan *p)
@@ -122,6 +126,7 @@ static void fft2_free(fft2_plan *p)
     free(p->line_in);
     free(p->line_out);
     free(p->scratch);
+    free(p->cols);
     memset(p, 0, sizeof(*p));
 }
 
@@ -136,14 +141,16 @@ static int fft2_init(fft2_plan *p, int H, int W)
     p->line_in = (cplx *)malloc(sizeof(cplx) * (size_t)n);
     p->line_out = (cplx *)malloc(sizeof(cplx) * (size_t)n);
     p->scratch = (cplx *)malloc(sizeof(cplx) * (size_t)n);
-    if (!p->twH || !p->twW || !p->line_in || !p->line_out || !p->scratch) {
+    p->cols = (cplx *)malloc(sizeof(cplx) * (size_t)H * COLS_PER_GATHER);
+    if (!p->twH || !p->twW || !p->line_in || !p->line_out || !p->scratch || !p->cols) {
         fft2_free(p);
         return NFSOR_ENOMEM;
     }
     return NFSOR_OK;
 }
 
-/* In-place unscaled forward 2-D DFT of a row-major H x W complex array: rows, then columns. */
+/* In-place unscaled forward 2-D DFT of a row-major H x W complex array: every row, then every
+ * column (columns are copied out a few at a time, transformed one by one and copied back). */
 static void fft2_forward(fft2_plan *p, cplx *a)
 {
     int H = p->H, W = p->W;
@@ -151,10 +158,16 @@ static void fft2_forward(fft2_plan *p, cplx *a)
         dft_rec(W, a + (size_t)y * W, 1, p->line_out, p->scratch, p->twW, W);
         memcpy(a + (size_t)y * W, p->line_out, sizeof(cplx) * (size_t)W);
     }
-    for (int x = 0; x < W; ++x) {
-        for (int y = 0; y < H; ++y) p->line_in[y] = a[(size_t)y * W + x];
-        dft_rec(H, p->line_in, 1, p->line_out, p->scratch, p->twH, H);
-        for (int y = 0; y < H; ++y) a[(size_t)y * W + x] = p->line_out[y];
+    for (int x0 = 0; x0 < W; x0 += COLS_PER_GATHER) {
+        int nc = W - x0 < COLS_PER_GATHER ? W - x0 : COLS_PER_GATHER;
+        for (int y = 0; y < H; ++y)
+            for (int c = 0; c < nc; ++c) p->cols[(size_t)c * H + y] = a[(size_t)y * W + x0 + c];
+        for (int c = 0; c < nc; ++c) {
+            dft_rec(H, p->cols + (size_t)c * H, 1, p->line_out, p->scratch, p->twH, H);
+            memcpy(p->cols + (size_t)c * H, p->line_out, sizeof(cplx) * (size_t)H);
+        }
+        for (int y = 0; y < H; ++y)
+            for (int c = 0; c < nc; ++c) a[(size_t)y * W + x0 + c] = p->cols[(size_t)c * H + y];
     }
 }
 
@@ -281,6 +294,33 @@ static int check_delays(const int32_t *delays, int nd)
 
 /* ---------------------------------------------------------------- structure function ----- */
 
+/* Adds |DFT(n_t - n_{t+tau})|^2 over the half plane into acc (work buffers a, b, F). */
+static void add_pair(const frame_src *s, fft2_plan *plan, int t, int tau, double *a, double *b, cplx *F, double *acc)
+{
+    int H = s->H, W = s->W, Wh = W / 2 + 1;
+    size_t nfull = (size_t)H * W;
+    load_frame(s, t, a);
+    load_frame(s, t + tau, b);
+    for (size_t i = 0; i < nfull; ++i) {
+        F[i].re = a[i] - b[i];
+        F[i].im = 0.0;
+    }
+    fft2_forward(plan, F);
+    for (int ky = 0; ky < H; ++ky)
+        for (int kx = 0; kx < Wh; ++kx) {
+            cplx v = F[(size_t)ky * W + kx];
+            acc[(size_t)ky * Wh + kx] += v.re * v.re + v.im * v.im;
+        }
+}
+
+/*
+ * Work is split over threads by pairs, not by delay: consecutive delays are grouped until the group
+ * has at least 4 pairs per thread, the group's pairs are listed in order (delay, then t ascending)
+ * and thread th takes the contiguous th-th share of the list.  A thread sums its pairs of one delay
+ * into its own partial ("segment"); the partials of a delay are then added in thread order, so the
+ * result does not depend on timing.  Pairs of one delay may be summed in any order (each is one
+ * term of the time average).
+ */
 static int sf_core(const frame_src *s, const int32_t *delays, int nd, int nq, int nthreads, double *D,
                    int64_t *bin_counts, int64_t *pair_counts, double *q_mean, double *D2d)
 {
@@ -310,18 +350,25 @@ static int sf_core(const frame_src *s, const int32_t *delays, int nd, int nq, in
     int nth = 1;
     (void)nthreads;
 #endif
-    double *Pth = (double *)calloc((size_t)nth * nhalf, sizeof(double));
-    if (!Pth) {
-        free(bin);
-        free(P);
-        return NFSOR_ENOMEM;
-    }
+    for (int j = 0; j < nd; ++j) pair_counts[j] = N - delays[j] > 0 ? N - delays[j] : 0;
     int err = 0;
-    for (int j = 0; j < nd; ++j) {
-        int tau = delays[j];
-        int npairs = N - tau > 0 ? N - tau : 0;
-        pair_counts[j] = npairs;
-        memset(Pth, 0, sizeof(double) * (size_t)nth * nhalf);
+    for (int j0 = 0; j0 < nd && !err;) {
+        /* the group j0 .. j1-1 and the first pair index of each of its delays */
+        long long tot = 0;
+        int j1 = j0;
+        while (j1 < nd && (tot < 4LL * nth || j1 == j0)) tot += pair_counts[j1++];
+        int ng = j1 - j0;
+        long long *first = (long long *)malloc(sizeof(long long) * (size_t)(ng + 1));
+        int nseg = nth + ng - 1; /* segment of (thread th, delay j) = th + (j - j0) */
+        double *seg = (double *)calloc((size_t)nseg * nhalf, sizeof(double));
+        if (!first || !seg) {
+            free(first);
+            free(seg);
+            err = 1;
+            break;
+        }
+        first[0] = 0;
+        for (int g = 0; g < ng; ++g) first[g + 1] = first[g] + pair_counts[j0 + g];
 #pragma omp parallel num_threads(nth)
         {
 #ifdef _OPENMP
@@ -329,7 +376,7 @@ static int sf_core(const frame_src *s, const int32_t *delays, int nd, int nq, in
 #else
             int tid = 0;
 #endif
-            double *mine = Pth + (size_t)tid * nhalf;
+            long long lo = tot * tid / nth, hi = tot * (tid + 1) / nth;
             double *a = (double *)malloc(sizeof(double) * nfull);
             double *b = (double *)malloc(sizeof(double) * nfull);
             cplx *F = (cplx *)malloc(sizeof(cplx) * nfull);
@@ -339,49 +386,46 @@ static int sf_core(const frame_src *s, const int32_t *delays, int nd, int nq, in
 #pragma omp atomic write
                 err = 1;
             }
-#pragma omp for schedule(static)
-            for (int t = 0; t < npairs; ++t) {
-                if (!ok) continue;
-                load_frame(s, t, a);
-                load_frame(s, t + tau, b);
-                for (size_t i = 0; i < nfull; ++i) {
-                    F[i].re = a[i] - b[i];
-                    F[i].im = 0.0;
-                }
-                fft2_forward(&plan, F);
-                for (int ky = 0; ky < H; ++ky)
-                    for (int kx = 0; kx < Wh; ++kx) {
-                        cplx v = F[(size_t)ky * W + kx];
-                        mine[(size_t)ky * Wh + kx] += v.re * v.re + v.im * v.im;
-                    }
+            int g = 0;
+            for (long long q = lo; ok && q < hi; ++q) {
+                while (q >= first[g + 1]) ++g;
+                int t = (int)(q - first[g]);
+                add_pair(s, &plan, t, delays[j0 + g], a, b, F, seg + (size_t)(tid + g) * nhalf);
             }
             if (ok) fft2_free(&plan);
             free(a);
             free(b);
             free(F);
         }
-        if (err) break;
-        /* thread partials in thread order: P_j(k) */
-        for (size_t i = 0; i < nhalf; ++i) {
-            double acc = 0.0;
-            for (int th = 0; th < nth; ++th) acc += Pth[(size_t)th * nhalf + i];
-            P[i] = acc;
-        }
-        double inv = npairs ? 1.0 / (double)npairs : 0.0;
-        if (D2d)
-            for (size_t i = 0; i < nhalf; ++i) D2d[(size_t)j * nhalf + i] = P[i] * inv;
-        for (int q = 0; q < nq; ++q) D[(size_t)j * nq + q] = 0.0;
-        for (int ky = 0; ky < H; ++ky)
-            for (int kx = 0; kx < Wh; ++kx) {
-                int32_t bb = bin[(size_t)ky * Wh + kx];
-                if (bb < 0) continue;
-                int w = (kx == 0 || kx == W / 2) ? 1 : 2;
-                D[(size_t)j * nq + bb] += w * P[(size_t)ky * Wh + kx] * inv;
+        for (int g = 0; g < ng && !err; ++g) {
+            int j = j0 + g;
+            /* partials of delay j in thread order (threads whose share overlaps its pairs) */
+            for (size_t i = 0; i < nhalf; ++i) P[i] = 0.0;
+            for (int th = 0; th < nth; ++th) {
+                long long lo = tot * th / nth, hi = tot * (th + 1) / nth;
+                if (hi <= first[g] || lo >= first[g + 1]) continue;
+                const double *sp = seg + (size_t)(th + g) * nhalf;
+                for (size_t i = 0; i < nhalf; ++i) P[i] += sp[i];
             }
-        for (int q = 0; q < nq; ++q)
-            D[(size_t)j * nq + q] = bin_counts[q] ? D[(size_t)j * nq + q] / (double)bin_counts[q] : 0.0;
+            long long npairs = pair_counts[j];
+            double inv = npairs ? 1.0 / (double)npairs : 0.0;
+            if (D2d)
+                for (size_t i = 0; i < nhalf; ++i) D2d[(size_t)j * nhalf + i] = P[i] * inv;
+            for (int q = 0; q < nq; ++q) D[(size_t)j * nq + q] = 0.0;
+            for (int ky = 0; ky < H; ++ky)
+                for (int kx = 0; kx < Wh; ++kx) {
+                    int32_t bb = bin[(size_t)ky * Wh + kx];
+                    if (bb < 0) continue;
+                    int w = (kx == 0 || kx == W / 2) ? 1 : 2;
+                    D[(size_t)j * nq + bb] += w * P[(size_t)ky * Wh + kx] * inv;
+                }
+            for (int q = 0; q < nq; ++q)
+                D[(size_t)j * nq + q] = bin_counts[q] ? D[(size_t)j * nq + q] / (double)bin_counts[q] : 0.0;
+        }
+        free(first);
+        free(seg);
+        j0 = j1;
     }
-    free(Pth);
     free(bin);
     free(P);
     return err ? NFSOR_ENOMEM : NFSOR_OK;
