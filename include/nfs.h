@@ -150,7 +150,9 @@ void *nfs_get_stream(const nfs_ctx *ctx);
 
 /* Option keys for nfs_set_option / nfs_get_option. */
 #define NFS_OPT_TIMING 1      /* 1 = record CUDA events around every kernel launch; 2 = around the
-                                  delay-update launches only (the least overhead); default 0 */
+                                  delay-update launches only (the least overhead); 3 = as 1, and
+                                  also keep each launch's start and end for nfs_get_timeline;
+                                  default 0 */
 #define NFS_OPT_BLOCK_FRAMES 2 /* read-only: K */
 #define NFS_OPT_RING_SLOTS 3   /* read-only: ring slots R = tau_max + K (FP32) or tau_max + 64 (FP64) */
 #define NFS_OPT_PITCH 4        /* read-only: complex values per spectrum row in HBM (>= W/2+1) */
@@ -185,6 +187,17 @@ int nfs_get_option(const nfs_ctx *ctx, int key, int64_t *value);
  */
 int nfs_get_timings(nfs_ctx *ctx, double *ms, int64_t *launches);
 int nfs_reset_timings(nfs_ctx *ctx);
+
+/*
+ * Timeline of the launches and host-to-device copies recorded with NFS_OPT_TIMING = 3 since the
+ * last nfs_reset_timings(), in issue order: stage[i] (NFS_STAGE_*), start_ms[i] and end_ms[i] in
+ * milliseconds from the first recorded launch (copies run on the context's copy stream, kernels on
+ * its compute stream; the times of both come from CUDA events on one device clock, so gaps and
+ * overlaps between the two streams can be read off).  Up to cap entries are written (any pointer
+ * may be NULL when cap is 0); *n receives the number recorded.  Synchronises.  Library tracing: the
+ * paper has no counterpart.  Errors: NFS_EINVAL (ctx or n NULL, cap < 0), sticky errors.
+ */
+int nfs_get_timeline(nfs_ctx *ctx, int32_t *stage, double *start_ms, double *end_ms, int64_t cap, int64_t *n);
 
 /*
  * Number of kernel launches the context has issued since creation (all stages, both paths).
@@ -352,26 +365,33 @@ int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *
  * (a framework's pool that has reserved the GPU), or an acquisition loop that must not take the
  * device-wide synchronisation that cudaMalloc / cudaFree can imply.
  *
- * nfs_structure_function_noalloc() computes, in one call, what nfs_create + nfs_push_frames_device
- * + nfs_structure_function compute for the fused FP32 path (same kernels, block K = 32), but
- * takes all of its scratch (spectrum ring, accumulators, twiddles, bin table, sums) from one
- * static device array of NFS_NOALLOC_SCRATCH_BYTES, and calls no cudaMalloc, cudaFree or other
- * allocating routine.
- *   dev_frames   n_frames (at most 2^30) frames in DEVICE memory, [n_frames][H][W] uint16, 2-byte
- *                aligned
+ * nfs_structure_function_noalloc() computes, in one call, the result nfs_create +
+ * nfs_push_frames_device + nfs_structure_function give for the fused FP32 path, but takes all of its
+ * scratch (spectrum ring, accumulators, twiddles, bin lists, sums) from one static device array of
+ * NFS_NOALLOC_SCRATCH_BYTES, and calls no cudaMalloc, cudaFree or other allocating routine.  Its
+ * steps differ from a context's in ways that change only FP32 rounding: the generic FFT kernels, the
+ * one-thread-per-mode delay update in blocks of 32 frames, and a reference image taken from the
+ * first 4 frames (a context takes it from its first copy chunk); the integer counts are identical.
+ *   dev_frames   n_frames (at most 2^30) frames in DEVICE memory of the CURRENT device,
+ *                [n_frames][H][W] uint16, 2-byte aligned
  *   H, W, delays, n_delays, n_qbins   as for nfs_create (delays and outputs are HOST memory)
- *   stream       cudaStream_t to run on (NULL = the legacy default stream); synchronised on return
+ *   stream       cudaStream_t to run on (NULL = the legacy default stream); the call synchronises it
+ *                before returning
  *   D, bin_counts, pair_counts        as for nfs_structure_function
+ * Returns NFS_EINVAL, before any GPU work, for the argument errors of nfs_create and when dev_frames
+ * is not device memory of the current device.
+ * Returns NFS_ESTATE, before any GPU work, when the stream is being captured (the call ends by
+ * synchronising its stream).
  * Returns NFS_EUNSUPPORTED, before any GPU work, also when 2 (n_qbins lcm(H, W))^2 >= 1.8e19 (its
  * device-side bin index works in 64-bit integers; nfs_create has no such limit).
  * Returns NFS_ETOOBIG, before any GPU work, when the sizes need more scratch than the array holds:
- * about 8 (tau_max + 32 + n_delays) H (W/2 + 1) bytes plus small tables (for example 128 x 128
+ * about 8 (tau_max + 32 + n_delays + 1) H (W/2 + 1) bytes plus small tables (for example 128 x 128
  * frames with tau_max = 50 and 50 delays need about 9 MB).
  * Notes for callers:
  *   - The array is a file-scope __device__ variable: every GPU that loads this library holds
  *     NFS_NOALLOC_SCRATCH_BYTES of device memory for it until the process exits.
- *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture.
+ *   - Every call looks up the array's device address (cudaGetSymbolAddress) with the current
+ *     device, so an address is never reused after the device's context was created again.
  *   - Every call shares the one array and it keeps the previous call's contents (the call clears
  *     what must start at zero).  Calls that overlap on the GPU -- two host threads, or two
  *     streams -- race on it and give wrong results; serialise them.

@@ -393,7 +393,11 @@ class OUFrameSource:
         return phi * self.field_scale
 
     def next_frames(self, n: int) -> torch.Tensor:
-        """The next n frames as an int16-storage tensor [n, H, W] holding 12-bit counts."""
+        """The next n frames as an int16-storage tensor [n, H, W] holding 12-bit counts (made a few
+        frames at a time: the integer draws need ~100 bytes of temporaries per pixel)."""
+        g = max(1, (1 << 23) // (self.H * self.W))
+        if n > g:
+            return torch.cat([self.next_frames(min(g, n - o)) for o in range(0, n, g)])
         t0 = self.t
         phi = self.fields(n)
         rate = self.profile * (1.0 + self.eps * phi)

@@ -85,6 +85,7 @@ def load_library(path: Optional[str] = None):
         "nfs_get_option": (I, [V, I, ctypes.POINTER(I64)]),
         "nfs_get_timings": (I, [V, V, V]),
         "nfs_reset_timings": (I, [V]),
+        "nfs_get_timeline": (I, [V, V, V, V, I64, ctypes.POINTER(I64)]),
         "nfs_launch_count": (I64, [V]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
         "nfs_out_of_core_plan": (I, [V, I, I64, I64, V, V, ctypes.POINTER(I), ctypes.POINTER(I64)]),
@@ -259,6 +260,19 @@ class NFS:
     def reset_timings(self):
         self._check(self._L.nfs_reset_timings(self._h), "nfs_reset_timings")
 
+    def timeline(self) -> list:
+        """[(stage name, start ms, end ms)] of every launch and copy since reset_timings (needs
+        set_option(OPT_TIMING, 3)); times from the first recorded launch."""
+        n = ctypes.c_int64(0)
+        self._check(self._L.nfs_get_timeline(self._h, None, None, None, 0, ctypes.byref(n)), "nfs_get_timeline")
+        m = n.value
+        st = np.zeros(max(m, 1), np.int32)
+        a = np.zeros(max(m, 1), np.float64)
+        e = np.zeros(max(m, 1), np.float64)
+        self._check(self._L.nfs_get_timeline(self._h, _ptr(st), _ptr(a), _ptr(e), m, ctypes.byref(n)),
+                    "nfs_get_timeline")
+        return [(STAGES[int(st[i])], float(a[i]), float(e[i])) for i in range(m)]
+
     def fit(self, A, B, Gamma, iters: int = 50, method: int = FIT_GAUSS_NEWTON, D=None):
         """Fit Eq. 1 per bin (nfs_fit); initial A, B, Gamma in, fitted arrays returned."""
         nq = self.n_qbins
@@ -276,6 +290,7 @@ def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) ->
 
     frames: CUDA tensor [n, H, W] of 2-byte integers.  Calls on one device must not overlap.
     """
+    import torch
     L = load_library()
     assert frames.is_cuda and frames.is_contiguous() and frames.element_size() == 2 and frames.dim() == 3
     n, H, W = frames.shape
@@ -283,9 +298,10 @@ def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) ->
     D = np.zeros((d.size, int(n_qbins)), np.float64)
     bc = np.zeros(int(n_qbins), np.int64)
     pc = np.zeros(d.size, np.int64)
-    rc = L.nfs_structure_function_noalloc(ctypes.c_void_p(frames.data_ptr()), int(n), int(H), int(W), _ptr(d),
-                                          int(d.size), int(n_qbins), ctypes.c_void_p(stream or None), _ptr(D),
-                                          _ptr(bc), _ptr(pc))
+    with torch.cuda.device(frames.device):  # the call runs on the current device: the frames' own
+        rc = L.nfs_structure_function_noalloc(ctypes.c_void_p(frames.data_ptr()), int(n), int(H), int(W), _ptr(d),
+                                              int(d.size), int(n_qbins), ctypes.c_void_p(stream or None), _ptr(D),
+                                              _ptr(bc), _ptr(pc))
     if rc != NFS_OK:
         raise NFSError(rc, "nfs_structure_function_noalloc")
     return dict(D=D, bin_counts=bc, pair_counts=pc)

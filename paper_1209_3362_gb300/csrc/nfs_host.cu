@@ -74,7 +74,16 @@ int harvest(nfs_ctx *c)
         CK(c, cudaEventElapsedTime(&ms, p.a, p.b));
         c->stage_ms[p.stage] += ms;
         c->stage_n[p.stage] += 1;
-        c->pool.push_back(p.a);
+        if (c->timing == 3) {
+            if (!c->tl_base) {
+                c->tl_base = p.a;  // kept (not pooled) until the next reset of the timings
+            }
+            float t0 = 0.f, t1 = 0.f;
+            CK(c, cudaEventElapsedTime(&t0, c->tl_base, p.a));
+            CK(c, cudaEventElapsedTime(&t1, c->tl_base, p.b));
+            c->timeline.push_back({p.stage, (double)t0, (double)t1});
+        }
+        if (p.a != c->tl_base) c->pool.push_back(p.a);
         c->pool.push_back(p.b);
     }
     c->pending.clear();
@@ -192,6 +201,7 @@ void free_all(nfs_ctx *c)
         cudaEventDestroy(p.b);
     }
     for (auto e : c->pool) cudaEventDestroy(e);
+    if (c->tl_base) cudaEventDestroy(c->tl_base);
     cudaFree(c->d_stage);
     for (auto e : c->ev_filled) cudaEventDestroy(e);
     for (auto e : c->ev_free) cudaEventDestroy(e);
@@ -766,7 +776,7 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
     if (rc) return rc;
     switch (key) {
         case NFS_OPT_TIMING:
-            if (v < 0 || v > 2) return NFS_EINVAL;
+            if (v < 0 || v > 3) return NFS_EINVAL;
             c->timing = (int)v;
             return NFS_OK;
         case NFS_OPT_FFT_CHUNK:
@@ -830,6 +840,24 @@ int nfs_reset_timings(nfs_ctx *c)
         c->stage_ms[s] = 0.0;
         c->stage_n[s] = 0;
     }
+    if (c->tl_base) c->pool.push_back(c->tl_base);
+    c->tl_base = nullptr;
+    c->timeline.clear();
+    return NFS_OK;
+}
+
+int nfs_get_timeline(nfs_ctx *c, int32_t *stage, double *start_ms, double *end_ms, int64_t cap, int64_t *n)
+{
+    if (!c || !n || cap < 0 || (cap > 0 && (!stage || !start_ms || !end_ms))) return NFS_EINVAL;
+    int rc = nfs_synchronize(c);
+    if (rc) return rc;
+    const int64_t m = (int64_t)c->timeline.size();
+    for (int64_t i = 0; i < std::min(m, cap); ++i) {
+        stage[i] = c->timeline[(size_t)i].stage;
+        start_ms[i] = c->timeline[(size_t)i].start_ms;
+        end_ms[i] = c->timeline[(size_t)i].end_ms;
+    }
+    *n = m;
     return NFS_OK;
 }
 

@@ -106,8 +106,14 @@ struct nfs_ctx {
     int err = NFS_OK;
     std::string errmsg;
 
-    int timing = 0;  // 1: events around every launch; 2: around delay-update launches only
+    int timing = 0;  // 1: events around every launch; 2: around delay-update launches only; 3: as 1 + timeline
     std::vector<nfs::host::TimedPair> pending;
+    cudaEvent_t tl_base = nullptr;  // timeline origin: the first event recorded since the last reset
+    struct TimelineEntry {
+        int stage;
+        double start_ms, end_ms;
+    };
+    std::vector<TimelineEntry> timeline;
     std::vector<cudaEvent_t> pool;
     double stage_ms[NFS_N_STAGES] = {};
     long long stage_n[NFS_N_STAGES] = {};
@@ -139,7 +145,7 @@ template <class F>
 int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    const bool on = c->timing == 1 || (c->timing == 2 && stage == NFS_STAGE_DELAY);
+    const bool on = c->timing == 1 || c->timing == 3 || (c->timing == 2 && stage == NFS_STAGE_DELAY);
     if (on) {
         a = pool_get(c);
         b = pool_get(c);

@@ -3,14 +3,14 @@
 // Some callers cannot allocate device memory while they run: a process whose device memory is
 // already owned by another allocator (a framework's memory pool holding the whole GPU), or an
 // acquisition loop that must not take the device-wide synchronisation cudaMalloc and cudaFree
-// can imply.  This entry point runs the same kernels as the context path (exact frame sums, the
-// r2c FFT, the fused FP32 delay update) with all of its scratch -- spectrum ring, accumulators,
-// tables, sums -- carved out of one file-scope __device__ array of NFS_NOALLOC_SCRATCH_BYTES.
-// Twiddles and the bin table are built on the device, and the binning kernel finds each bin's
-// modes by scanning a per-mode bin index instead of a host-built list, so no host heap is used
-// either.  The paper has no counterpart to this entry point.
+// can imply.  This entry point runs the steps of the context path (exact frame sums, the r2c FFT
+// with the generic kernels, the one-thread-per-mode FP32 delay update in blocks of 32 frames, the
+// CSR binning kernel) with all of its scratch -- spectrum ring, accumulators, tables, sums -- carved
+// out of one file-scope __device__ array of NFS_NOALLOC_SCRATCH_BYTES.  Twiddles and the bin table
+// are built on the device (the bin lists by a stable counting placement in mode order, so the
+// binned sums do not depend on timing), so no host heap is used either.  The paper has no
+// counterpart to this entry point.
 #include <algorithm>
-#include <mutex>
 
 #include "nfs_internal.cuh"
 
@@ -23,27 +23,16 @@ namespace {
 
 constexpr int kNaBlock = 32;  // K of the fused delay update (same default as a context)
 constexpr int kNaChunk = 4;   // frames per FFT launch pair
-constexpr int kNaMaxDevices = 64;
-
-std::mutex g_na_mutex;
-void *g_na_ptr[kNaMaxDevices] = {};
-
-// The array's device address for the current device.  Host code must not pass the symbol itself
-// to a kernel: on the host it names a host-side stand-in, not device memory.
+// The array's device address on the current device, looked up on every call with that device
+// current: host code must not pass the symbol itself to a kernel (on the host it names a host-side
+// stand-in, not device memory), and an address kept from an earlier call could be stale after the
+// device's context was torn down and created again (the module, and the array with it, reloads).
 cudaError_t scratch_address(void **out)
 {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_na_ptr[dev] = p;
-    }
-    *out = g_na_ptr[dev];
+    *out = p;
     return cudaSuccess;
 }
 
@@ -86,40 +75,50 @@ __global__ void k_na_bin_index(int *bin_of, Geometry g, int nq, long long L)
     }
 }
 
-// counts[b] = sum of the weights of bin b (integer adds: exact in any order).
-__global__ void k_na_bin_counts(const int *bin_of, size_t M, long long *counts)
+// counts[b] = sum of the weights of bin b, nmodes[b] = its number of modes (integer adds: exact in
+// any order).
+__global__ void k_na_bin_counts(const int *bin_of, size_t M, long long *counts, int *nmodes)
 {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += (size_t)gridDim.x * blockDim.x) {
         const int c = bin_of[i];
-        if (c >= 0) atomicAdd((unsigned long long *)&counts[c >> 1], (c & 1) ? 2ull : 1ull);
+        if (c >= 0) {
+            atomicAdd((unsigned long long *)&counts[c >> 1], (c & 1) ? 2ull : 1ull);
+            atomicAdd(&nmodes[c >> 1], 1);
+        }
     }
 }
 
-// D[j][b] as in the context path; one CTA per (bin, delay) scans every mode in a fixed order.
-__global__ void __launch_bounds__(128) k_na_bin(const float2 *__restrict__ acc, const int *__restrict__ bin_of,
-                                                size_t M, int nq, const long long *__restrict__ pairs,
-                                                const long long *__restrict__ counts, double *__restrict__ D)
+// off[b] = modes of bins 0 .. b-1 (exclusive prefix sum, off[nq] = total); cursor[b] = off[b].
+__global__ void k_na_bin_offsets(const int *nmodes, int nq, int *off, int *cursor)
 {
-    const int b = blockIdx.x, j = blockIdx.y;
-    const float2 *aj = acc + (size_t)j * M;
-    double s = 0.0;
-    for (size_t i = threadIdx.x; i < M; i += blockDim.x) {
-        const int c = __ldg(bin_of + i);
-        if (c >= 0 && (c >> 1) == b) {
-            const float2 v = aj[i];
-            const double x = (double)v.x - (double)v.y;
-            s += (c & 1) ? 2.0 * x : x;
-        }
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int acc = 0;
+    for (int b = 0; b < nq; ++b) {
+        off[b] = acc;
+        cursor[b] = acc;
+        acc += nmodes[b];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    __shared__ double part[4];
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double tot = (part[0] + part[1]) + (part[2] + part[3]);
-        const long long np = pairs[j], c = counts[b];
-        D[(size_t)j * nq + b] = (np > 0 && c > 0) ? tot / ((double)np * (double)c) : 0.0;
+    off[nq] = acc;
+}
+
+// The bin lists in CSR form, entries (mode << 1) | (weight == 2), each bin's modes in increasing
+// mode order (a stable counting placement): one warp walks the modes 32 at a time, the lanes of one
+// bin take consecutive places by their rank among that bin's lanes, and the lowest of them then
+// advances the bin's cursor.
+__global__ void k_na_bin_place(const int *__restrict__ bin_of, size_t M, int *cursor, int *modes)
+{
+    if (blockIdx.x != 0 || threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const unsigned lt = (1u << lane) - 1u;
+    for (size_t base = 0; base < M; base += 32) {
+        const size_t i = base + lane;
+        const int c = i < M ? bin_of[i] : -1;
+        const int b = c >= 0 ? (c >> 1) : -1;
+        const unsigned same = __match_any_sync(0xffffffffu, b);
+        if (b >= 0) modes[cursor[b] + __popc(same & lt)] = (int)((i << 1) | (size_t)(c & 1));
+        __syncwarp();
+        if (b >= 0 && (same & lt) == 0) cursor[b] += __popc(same);
+        __syncwarp();
     }
 }
 
@@ -179,6 +178,26 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     const int nd = n_delays, nq = n_qbins;
     const int R = delays[nd - 1] + kNaBlock;
 
+    // Frames must be this device's memory (another device's would be read through a peer pointer).
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) return NFS_ECUDA;
+    if (n_frames > 0) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, dev_frames) != cudaSuccess) {
+            cudaGetLastError();
+            return NFS_EINVAL;
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != cur)
+            return NFS_EINVAL;
+    }
+    // The call synchronises its stream before it returns, which stream capture does not allow.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return NFS_ESTATE;
+    }
+    if (cap != cudaStreamCaptureStatusNone) return NFS_ESTATE;
+
     // Scratch layout, every piece 256-byte aligned.
     size_t off = 0;
     const size_t o_ring = carve(&off, (size_t)R * g.M * sizeof(float2));
@@ -191,6 +210,10 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     const size_t o_twp = carve(&off, sizeof(float2) * (size_t)g.Wh);
     const size_t o_bin = carve(&off, sizeof(int) * g.M);
     const size_t o_cnt = carve(&off, sizeof(long long) * (size_t)nq);
+    const size_t o_nmodes = carve(&off, sizeof(int) * (size_t)nq);
+    const size_t o_boff = carve(&off, sizeof(int) * ((size_t)nq + 1));
+    const size_t o_cursor = carve(&off, sizeof(int) * (size_t)nq);
+    const size_t o_bmodes = carve(&off, sizeof(int) * g.M);
     const size_t o_pairs = carve(&off, sizeof(long long) * (size_t)nd);
     const size_t o_del = carve(&off, sizeof(int) * (size_t)nd);
     const size_t o_D = carve(&off, sizeof(double) * (size_t)nd * nq);
@@ -208,12 +231,15 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     float2 *twr = (float2 *)(base + o_twr), *twc = (float2 *)(base + o_twc), *twp = (float2 *)(base + o_twp);
     int *bin_of = (int *)(base + o_bin);
     long long *cnt = (long long *)(base + o_cnt), *pairs = (long long *)(base + o_pairs);
+    int *nmodes = (int *)(base + o_nmodes), *boff = (int *)(base + o_boff), *cursor = (int *)(base + o_cursor);
+    int *bmodes = (int *)(base + o_bmodes);
     int *dd = (int *)(base + o_del);
     double *Dd = (double *)(base + o_D);
 
     // The array keeps the previous call's contents: zero what accumulates.
     NA_CK(cudaMemsetAsync(acc, 0, (size_t)nd * g.M * sizeof(float2), s));
     NA_CK(cudaMemsetAsync(cnt, 0, sizeof(long long) * (size_t)nq, s));
+    NA_CK(cudaMemsetAsync(nmodes, 0, sizeof(int) * (size_t)nq, s));
     for (int j = 0; j < nd; ++j) pair_counts[j] = n_frames > delays[j] ? n_frames - delays[j] : 0;
     NA_CK(cudaMemcpyAsync(dd, delays, sizeof(int) * (size_t)nd, cudaMemcpyHostToDevice, s));
     NA_CK(cudaMemcpyAsync(pairs, pair_counts, sizeof(long long) * (size_t)nd, cudaMemcpyHostToDevice, s));
@@ -223,7 +249,9 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
     const long long L = (long long)H / gcd_na(H, W) * W;
     NA_CK(cudaMemsetAsync(bin_of, 0xff, sizeof(int) * g.M, s));
     k_na_bin_index<<<256, 256, 0, s>>>(bin_of, g, nq, L);
-    k_na_bin_counts<<<256, 256, 0, s>>>(bin_of, g.M, cnt);
+    k_na_bin_counts<<<256, 256, 0, s>>>(bin_of, g.M, cnt, nmodes);
+    k_na_bin_offsets<<<1, 1, 0, s>>>(nmodes, nq, boff, cursor);
+    k_na_bin_place<<<1, 32, 0, s>>>(bin_of, g.M, cursor, bmodes);
     NA_CK(cudaGetLastError());
 
     long long done = 0, processed = 0;
@@ -245,8 +273,7 @@ extern "C" int nfs_structure_function_noalloc(const uint16_t *dev_frames, int n_
             processed = done;
         }
     }
-    k_na_bin<<<dim3(nq, nd), 128, 0, s>>>(acc, bin_of, g.M, nq, pairs, cnt, Dd);
-    NA_CK(cudaGetLastError());
+    NA_CK(launch_bin<float2>(acc, g.M, nd, nq, boff, bmodes, pairs, cnt, Dd, s));
     NA_CK(cudaMemcpyAsync(D, Dd, sizeof(double) * (size_t)nd * nq, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaMemcpyAsync(bin_counts, cnt, sizeof(long long) * (size_t)nq, cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));

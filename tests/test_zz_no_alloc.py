@@ -40,6 +40,9 @@ def test_noalloc_matches_context_path_on_two_calls_in_a_row():
     cases = [
         (S.OUFrameSource(128, 128, 0.5, seed=41).frames_numpy(80), list(range(1, 21)) + [40, 79], 64),
         (S.OUFrameSource(96, 64, 2.0, seed=42).frames_numpy(50), [1, 2, 3, 5, 8, 30, 60], 24),
+        # 100 frames through a ring of R = 5 + 32 = 37 slots: the ring wraps, and 4-frame FFT chunks
+        # straddle its last and first slots (37 is not a multiple of 4)
+        (S.OUFrameSource(64, 64, 1.0, seed=43).frames_numpy(100), [1, 2, 3, 5], 16),
     ]
     for frames, delays, nq in cases:
         dev = torch.from_numpy(frames.view(np.int16)).cuda()
@@ -57,3 +60,17 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(P.NFSError) as e:
         P.structure_function_noalloc(dev, [1, 100], 16)
     assert e.value.status == P.NFS_ETOOBIG
+
+
+def test_noalloc_leaves_device_memory_unchanged():
+    """After a first call (which loads the library's kernels and its static array), further calls
+    change neither PyTorch's allocations nor the device's free memory."""
+    fr = torch.from_numpy(S.OUFrameSource(64, 64, 1.0, seed=44).frames_numpy(40).view(np.int16)).cuda()
+    P.structure_function_noalloc(fr, [1, 2, 7], 16)
+    torch.cuda.synchronize()
+    alloc0, free0 = torch.cuda.memory_allocated(), torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        P.structure_function_noalloc(fr, [1, 2, 7], 16)
+    torch.cuda.synchronize()
+    assert torch.cuda.memory_allocated() == alloc0
+    assert torch.cuda.mem_get_info()[0] == free0
