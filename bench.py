@@ -20,8 +20,11 @@ radial binning, ending with the binned D(q, tau) copied to the host.
 --workload ragged48 (48 sequences of uneven shapes, one batch) and --workload roi2048 (2048x2048
 frames cut into 16 regions of interest) time the batch paths with frames resident in HBM.
 --impl reference times the FP64 CPU oracle alone (rank 0 only), each step a bounded sample.
-Multi-GPU: each rank analyses its own independent sequence (replicas, weak scaling), no collective
-on the data path; the timing is the max over ranks.
+Multi-GPU (torchrun, N > 1): the mode-slab split -- every rank takes all frames of the one sequence
+but holds 1/N of the spectrum's modes (nfs_create_slab); the ranks' shares of the binned D are
+summed by one all-reduce of n_delays x n_qbins doubles (gloo, host memory) inside the timed step:
+strong scaling, value = frames of the sequence per second; the timing is the max over ranks.
+--replicas instead runs an independent sequence per rank with no collective (weak scaling).
 """
 from __future__ import annotations
 
@@ -148,23 +151,56 @@ def delay_block_bytes(delays, N, K, M):
     return total, launches, pairs
 
 
-def oracle_sample(frames_host, budget_s, cores):
-    """Time the FP64 oracle on the first n frames with every delay 1..n-1; n sized from a one-pair probe."""
+def sample_shape(job_delays, target_pairs, n_max):
+    """A bounded sample of the job for the oracle: its first n frames with the job's own delays
+    below n (a prefix of its list), n the largest with at most target_pairs pairs (at least 2)."""
+    n = 2
+    while n < n_max:
+        m = n + 1
+        if sum(m - d for d in job_delays if d < m) > target_pairs:
+            break
+        n = m
+    delays = [d for d in job_delays if d < n] or [1]
+    return n, delays, sum(max(0, n - d) for d in delays)
+
+
+def oracle_sample(frames_host, job_delays, budget_s, cores, repeats=1, warmup=0):
+    """Time the FP64 oracle (all cores; its threads split the sample's pairs across delays) on a
+    sample sized from a one-pair probe to about budget_s; returns (n, delays, pairs, seconds per run)."""
     import oracle
     oracle.build()
-    H, W = frames_host.shape[1:]
     t = time.perf_counter()
     oracle.structure_function(frames_host[:2], [1], 8, nthreads=1)
     per_pair = time.perf_counter() - t
-    target_pairs = max(3, int(budget_s * cores / max(per_pair, 1e-6)))
-    n = 2
-    while (n + 1) * n // 2 <= target_pairs and n < frames_host.shape[0]:
-        n += 1
-    delays = list(range(1, n))
-    t = time.perf_counter()
-    oracle.structure_function(frames_host[:n], delays, 8, nthreads=cores)
-    dt = time.perf_counter() - t
-    return n, n * (n - 1) // 2, dt
+    n, delays, pairs = sample_shape(job_delays, max(3, int(budget_s * cores / max(per_pair, 1e-6))),
+                                    frames_host.shape[0])
+    for _ in range(warmup):
+        oracle.structure_function(frames_host[:n], delays, 8, nthreads=cores)
+    times = []
+    for _ in range(max(1, repeats)):
+        t = time.perf_counter()
+        oracle.structure_function(frames_host[:n], delays, 8, nthreads=cores)
+        times.append(time.perf_counter() - t)
+    return n, delays, pairs, times
+
+
+def golden_parity(w, D, pair_counts, bin_counts, checksums):
+    """Largest relative difference of D from the FP64 oracle's stored values for this workload
+    (tests/golden/<workload>_oracle.npz, written by tests/golden/make_golden.py from the same
+    seeded frames), or None when there is no fixture or the frames differ from it."""
+    p = os.path.join(ROOT, "tests", "golden", f"{w.name}_oracle.npz")
+    if not os.path.exists(p):
+        return None
+    z = np.load(p)
+    if int(z["N"]) != w.N or int(z["H"]) != w.H or int(z["W"]) != w.W or int(z["seed"]) != w.seed:
+        return None
+    diff = int(np.count_nonzero(np.any(z["frame_checksums"] != checksums, axis=1)))
+    idx = z["delay_index"]
+    ref, got = z["D"], D[idx]
+    m = (z["bin_counts"][None, :] > 0) & (z["pair_counts"][:, None] > 0)
+    exact = bool(np.array_equal(bin_counts, z["bin_counts"]) and np.array_equal(pair_counts[idx], z["pair_counts"]))
+    return {"max_rel_err": float(np.max(np.abs(got[m] - ref[m]) / np.abs(ref[m]))), "delays_checked": int(idx.size),
+            "counts_exact": exact, "frames_differing": diff, "fixture": os.path.relpath(p, ROOT)}
 
 
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
@@ -183,30 +219,21 @@ def job_value(world: int, frames_per_rank: int, step_ms: float) -> float:
 
 
 def run_reference(args, w):
-    """The FP64 CPU oracle alone, each step a bounded sample; rank 0 prints."""
+    """The FP64 CPU oracle alone, each step a bounded sample of the job (its first frames and its
+    own delays below that count); rank 0 prints."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    import torch
     cores = len(os.sched_getaffinity(0))
-    src = S.workload_source(w, device="cpu", dtype=torch.float32)
-    n_s = 12
-    fr = src.frames_numpy(n_s)
-    import oracle
-    oracle.build()
-    pairs_per_step = n_s * (n_s - 1) // 2
-    for _ in range(max(args.warmup, 0)):  # untimed warm-up steps: the same sample
-        oracle.structure_function(fr, list(range(1, n_s)), 8, nthreads=cores)
-    times = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        oracle.structure_function(fr, list(range(1, n_s)), 8, nthreads=cores)
-        times.append(time.perf_counter() - t)
-    per_pair = sum(times) / (len(times) * pairs_per_step)
+    src = S.workload_source(w, device="cpu")
+    fr = src.frames_numpy(min(w.N, 40))
+    n, delays, pairs, times = oracle_sample(fr, w.delays, args.ref_budget, cores, repeats=args.steps,
+                                            warmup=max(args.warmup, 0))
+    per_pair = sum(times) / (len(times) * pairs)
     value = w.N / (per_pair * w.pair_total)
     ms = 1000.0 * sum(times) / len(times)
-    sample = (f"{n_s} frames of {w.H}x{w.W}, delays 1..{n_s - 1} ({pairs_per_step} pair FFTs) per step; "
-              f"extrapolated by pair count to the job's {w.pair_total} pairs")
+    sample = (f"first {n} frames of {w.H}x{w.W} with the job's delays below {n} ({len(delays)} delays, {pairs} "
+              f"pair FFTs) per step; extrapolated by pair count to the job's {w.pair_total} pairs")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -231,10 +258,12 @@ def main():
     ap.add_argument("--delays", type=int, default=0, help="use delays 1..n (profiling cases; not a bench value)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--delay-variant", type=int, default=0, help="fused delay kernel variant (0 = default)")
+    ap.add_argument("--replicas", action="store_true", help="N > 1: independent sequences per rank (weak scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=4.0, help="seconds of oracle work per reference step")
     args = ap.parse_args()
     if args.workload in S.RAGGED_WORKLOADS:
         return run_ragged(args, S.RAGGED_WORKLOADS[args.workload])
@@ -256,9 +285,13 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = None
+    gloo = None
+    slabs = world > 1 and not args.replicas
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if slabs:
+            gloo = dist.new_group(backend="gloo")  # the one exchange: bin shares in host memory
 
     def barrier():
         if dist is not None:
@@ -273,16 +306,22 @@ def main():
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = n_sm * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s
 
-    # ---- inputs: the rank's own sequence, generated on its GPU, resident in HBM
-    src = S.OUFrameSource(w.H, w.W, w.Dc, w.gamma0, eps=w.eps, seed=w.seed + 7919 * rank, device="cuda",
-                          dtype=torch.float32)
+    # ---- inputs: the rank's own sequence, generated on its GPU, resident in HBM.  Rank 0 analyses
+    # the workload's own seeded frames (the counter-based generator gives the same frames on the
+    # CPU, where the oracle's stored values were computed); other ranks take other seeds.
+    seed = w.seed if (slabs or rank == 0) else w.seed + 7919 * rank
+    src = S.OUFrameSource(w.H, w.W, w.Dc, w.gamma0, eps=w.eps, seed=seed, device="cuda")
     frames = torch.empty((w.N, w.H, w.W), dtype=torch.int16, device="cuda")
+    checksums = np.zeros((w.N, 2), np.int64)
     gb = 16
+    t_gen = time.perf_counter()
     for o in range(0, w.N, gb):
         n = min(gb, w.N - o)
         frames[o:o + n] = src.next_frames(n)
+        checksums[o:o + n] = S.frame_checksums(frames[o:o + n])
     del src
     torch.cuda.synchronize()
+    t_gen = time.perf_counter() - t_gen
     # the pinned host copy for the end-to-end run, allocated and filled before the library's own
     # allocations (as an acquisition program would hold its frame buffer)
     host = None
@@ -290,17 +329,24 @@ def main():
         host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
         host.copy_(frames)
 
-    ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
+    if slabs:
+        ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, slab=rank, n_slabs=world)
+    else:
+        ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
     if args.delay_variant:
         ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
-    M = (w.H * (w.W // 2 + 1) + 15) // 16 * 16  # modes per spectrum (column-major, padded to 16-mode tiles)
+    M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
     stream = torch.cuda.ExternalStream(ctx.stream)
+
+    def finish():
+        r = ctx.structure_function()
+        return P.reduce_slabs(r, group=gloo) if slabs else r
 
     def step():
         ctx.reset()
         ctx.push_frames_device(frames)
-        return ctx.structure_function()
+        return finish()
 
     for _ in range(max(args.warmup, 0)):
         step()
@@ -326,7 +372,7 @@ def main():
     launches = ctx.launch_count - l0
     dev_ms = ev0.elapsed_time(ev1)
     step_ms = ranks_max(max(dev_ms, 1000.0 * wall) / args.steps)
-    value = job_value(world, w.N, step_ms)
+    value = job_value(1 if slabs else world, w.N, step_ms)
     tim = ctx.timings()
     D32 = res["D"]
 
@@ -335,7 +381,7 @@ def main():
     # moved once per block) lies above the FP32 ridge point, so the roofline that bounds it is the
     # FP32 ALU peak; the HBM fraction the metric asks for is reported beside it.
     alg_bytes, n_launch, pairs = delay_block_bytes(w.delays, w.N, K, M)
-    modes = w.H * (w.W // 2 + 1)
+    modes = M if slabs else w.H * (w.W // 2 + 1)  # a slab's share of the modes on this rank
     alg_flops = FLOPS_PER_PAIR_MODE * pairs * modes
     delay_ms, delay_n = tim["delay"]
     per_launch_ms = delay_ms / max(delay_n, 1)
@@ -386,7 +432,7 @@ def main():
         def step_host():
             ctx.reset()
             ctx.push_frames(host)
-            return ctx.structure_function()
+            return finish()
 
         step_host()
         barrier()
@@ -394,7 +440,8 @@ def main():
         for _ in range(args.steps):
             step_host()
         e2e_s = ranks_max((time.perf_counter() - t0) / args.steps)
-        e2e = {"value": job_value(world, w.N, 1000.0 * e2e_s), "unit": "frames/s", "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
+        e2e = {"value": job_value(1 if slabs else world, w.N, 1000.0 * e2e_s), "unit": "frames/s",
+               "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
                "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
         # the copy engines' rate from this process's page-locked buffer (1 GiB, alone on the GPU):
         # the end-to-end rate depends on it, and it varies with the box's state
@@ -413,7 +460,7 @@ def main():
 
     # ---- the plain unfused FP64 GPU path, one pass on the same frames
     plain = None
-    if not args.no_f64:
+    if not args.no_f64 and rank == 0:
         if frames is None:
             frames = host.cuda() if e2e is not None else None
         c64 = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f64")
@@ -426,10 +473,10 @@ def main():
         r64 = c64.structure_function()
         e1.record(s64)
         e1.synchronize()
-        ms64 = ranks_max(e0.elapsed_time(e1))
+        ms64 = e0.elapsed_time(e1)
         m = (r64["bin_counts"][None, :] > 0) & (r64["pair_counts"][:, None] > 0)
         err = float(np.max(np.abs(D32[m] - r64["D"][m]) / np.abs(r64["D"][m])))
-        plain = {"value": job_value(world, w.N, ms64), "unit": "frames/s", "ms_per_pass": ms64,
+        plain = {"value": job_value(1, w.N, ms64), "unit": "frames/s", "ms_per_pass": ms64,
                  "max_rel_err_f32_vs_f64": err}
         c64.close()
 
@@ -438,27 +485,30 @@ def main():
     if not args.no_cpu and rank == 0:
         if frames is None:
             frames = host.cuda()
-        nmax = 40
-        fh = frames[:nmax].cpu().numpy().view(np.uint16)
+        fh = frames[:64].cpu().numpy().view(np.uint16)
         cores = len(os.sched_getaffinity(0))
-        n_s, p_s, dt = oracle_sample(fh, args.cpu_budget, cores)
+        n_s, d_s, p_s, ts = oracle_sample(fh, w.delays, args.cpu_budget, cores)
+        dt = ts[0]
         cpu = {"value": w.N / (dt / p_s * w.pair_total), "unit": "frames/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {n_s} frames, delays 1..{n_s - 1}: {p_s} pair FFTs of {w.H}x{w.W} in {dt:.1f} s, "
-                         f"extrapolated by pair count to {w.pair_total} pairs"}
+               "sample": f"first {n_s} frames with the job's delays below {n_s} ({len(d_s)} delays): {p_s} pair "
+                         f"FFTs of {w.H}x{w.W} in {dt:.1f} s, extrapolated by pair count to {w.pair_total} pairs"}
+    parity = golden_parity(w, D32, res["pair_counts"], res["bin_counts"], checksums) if rank == 0 else None
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+                "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+                "scaling": "strong" if slabs else ("weak" if world > 1 else "strong"),
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
-                           "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (frames "
+                           "parallelism": (f"mode-slabs{world}" if slabs else f"replicas{world}"),
+                           "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "
                            f"{ctx_bytes(w, K, M) / 1e9:.1f} GB per rank)"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "clocks": clk.summary(), "plain_f64_gpu": plain, "stage_ms_per_step": stage_ms,
                 "stage_gbs": stage_gbs, "hbm_bound": hbm_bound, "pass_bound": pass_bound,
-                "delay_pairs_per_step": pairs}
+                "delay_pairs_per_step": pairs, "parity_vs_oracle": parity, "input_generation_s": t_gen}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -77,6 +77,31 @@ int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins
                   nfs_ctx **out);
 
 /*
+ * ---------------------------------------------------------------- mode slabs (several GPUs)
+ * Eq. 1 is evaluated independently at every wave vector q, so the spectrum can be split by mode:
+ * a slab context takes every frame (mean, reference image and row transforms of whole frames, as
+ * any context) but keeps only its slab's share of the modes -- the column transforms of the
+ * column pairs that hold them, their ring slots, their accumulators and their terms of every bin.
+ * The bin counts C_b stay those of the whole plane, so each slab's D_b(tau) is its share of the
+ * azimuthal average and the results of the n_slabs slabs of one frame sequence ADD UP to the
+ * whole context's D (up to FP64 rounding of the sum; pair counts, bin counts and q_mean are
+ * those of the whole spectrum).  One context per GPU with a sum over GPUs of D (n_delays x n_qbins
+ * doubles) is the only exchange.  The paper runs one GPU; the split is this library's.
+ *
+ * nfs_create_slab(): as nfs_create (fused FP32 path, K = 512) for slab `slab` of n_slabs, the
+ * 16-mode tiles of the column-major mode order split evenly and in order.  nfs_export_spectrum on a
+ * slab context writes 0 at the modes of other slabs (the exports of all slabs also add up).
+ * Errors: NFS_EINVAL also for n_slabs < 1, slab outside [0, n_slabs) or more slabs than tiles.
+ *
+ * nfs_slab_range(): host only; first_mode and n_modes of the slab in the column-major order
+ * k = k_x H + k_y (n_modes a multiple of 16; the last slab may end in padding modes past H(W/2+1)).
+ * Errors: NFS_EINVAL (NULL outputs, bad slab), NFS_EUNSUPPORTED (shape).
+ */
+int nfs_create_slab(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int slab, int n_slabs,
+                    nfs_ctx **out);
+int nfs_slab_range(int H, int W, int slab, int n_slabs, int64_t *first_mode, int64_t *n_modes);
+
+/*
  * The radial bin table of an H x W frame with n_qbins bins (the rule above; Fig. 1e,f's azimuthal
  * average), computed on the host with no device call.  Caller-owned outputs:
  *   bin_of_mode  [H][W/2+1] int32, row-major over (k_y, k_x): the bin of each half-plane mode or -1
@@ -168,6 +193,8 @@ void *nfs_get_stream(const nfs_ctx *ctx);
                                       stops issuing copies from this group on, so a consumer's bounded
                                       wait runs out (~2 s) and the call returns NFS_ETIMEOUT; checks
                                       the failure path without faulting the GPU */
+#define NFS_OPT_SLAB_FIRST_MODE 10 /* read-only: first mode (column-major order) of a slab context */
+#define NFS_OPT_SLAB_MODES 11      /* read-only: modes held (the slab's share, a multiple of 16) */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);
 int nfs_get_option(const nfs_ctx *ctx, int key, int64_t *value);
 
@@ -198,6 +225,16 @@ int nfs_reset_timings(nfs_ctx *ctx);
  * paper has no counterpart.  Errors: NFS_EINVAL (ctx or n NULL, cap < 0), sticky errors.
  */
 int nfs_get_timeline(nfs_ctx *ctx, int32_t *stage, double *start_ms, double *end_ms, int64_t cap, int64_t *n);
+
+/*
+ * Measuring hook of the fused delay kernel: in a library built with NFS_DELAY_PROFILE
+ * (buildlib.build(profile=True)), the clock cycles its warp roles spent by phase, summed over every
+ * launch since the last reset (consumer total, copy-group waits, partial-buffer waits, pair
+ * arithmetic, hand-overs, writer total, writer waits, producer waits, prologue, epilogue, tile
+ * passes): out[0 .. n) are written and the count of values is returned; reset != 0 clears them.
+ * A normal build returns NFS_EUNSUPPORTED.  Library tracing: the paper has no counterpart.
+ */
+int nfs_delay_profile(unsigned long long *out, int n, int reset);
 
 /*
  * Number of kernel launches the context has issued since creation (all stages, both paths).

@@ -394,8 +394,9 @@ class OUFrameSource:
 
     def next_frames(self, n: int) -> torch.Tensor:
         """The next n frames as an int16-storage tensor [n, H, W] holding 12-bit counts (made a few
-        frames at a time: the integer draws need ~100 bytes of temporaries per pixel)."""
-        g = max(1, (1 << 23) // (self.H * self.W))
+        frames at a time: the integer draws need ~150 bytes of temporaries per pixel)."""
+        cap = (1 << 26) if self.device.type == "cuda" else (1 << 23)  # pixels per group (device memory is ample)
+        g = max(1, cap // (self.H * self.W))
         if n > g:
             return torch.cat([self.next_frames(min(g, n - o)) for o in range(0, n, g)])
         t0 = self.t

@@ -38,6 +38,8 @@ OPT_FFT_CHUNK = 6
 OPT_DELAY_VARIANT = 7
 OPT_FFT_GENERIC = 8
 OPT_TEST_STALL_GROUP = 9
+OPT_SLAB_FIRST_MODE = 10
+OPT_SLAB_MODES = 11
 FIT_GAUSS_NEWTON = 0
 FIT_ADAM = 1
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
@@ -70,6 +72,8 @@ def load_library(path: Optional[str] = None):
     sig = {
         "nfs_create": (I, [I, I, V, I, I, PP]),
         "nfs_create_ex": (I, [I, I, V, I, I, I, I, PP]),
+        "nfs_create_slab": (I, [I, I, V, I, I, I, I, PP]),
+        "nfs_slab_range": (I, [I, I, I, I, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
         "nfs_push_frames": (I, [V, V, I]),
         "nfs_push_frames_device": (I, [V, V, I]),
         "nfs_structure_function": (I, [V, V, V, V, V]),
@@ -87,6 +91,7 @@ def load_library(path: Optional[str] = None):
         "nfs_reset_timings": (I, [V]),
         "nfs_get_timeline": (I, [V, V, V, V, I64, ctypes.POINTER(I64)]),
         "nfs_launch_count": (I64, [V]),
+        "nfs_delay_profile": (I, [V, I, I]),
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
         "nfs_out_of_core_plan": (I, [V, I, I64, I64, V, V, ctypes.POINTER(I), ctypes.POINTER(I64)]),
         "nfs_delay_schedule": (I, [V, I, I, V, V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
@@ -144,17 +149,27 @@ class NFS:
     """One analysis context: frames in, binned structure function D_b(tau) out (Eq. 1, Fig. 1e,f)."""
 
     def __init__(self, H: int, W: int, delays: Sequence[int], n_qbins: int, path: str = "f32",
-                 block_frames: int = 0):
+                 block_frames: int = 0, slab: int = 0, n_slabs: int = 1):
+        """slab, n_slabs: keep only that share of the modes (nfs_create_slab; the D of all slabs of
+        one frame sequence add up to the whole D, see reduce_slabs)."""
         self._L = load_library()
         self.H, self.W = int(H), int(W)
         self.delays = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
         self.n_qbins = int(n_qbins)
         self.path = {"f32": PATH_FUSED_F32, "f64": PATH_PLAIN_F64}[path]
         h = ctypes.c_void_p()
-        rc = self._L.nfs_create_ex(self.H, self.W, _ptr(self.delays), int(self.delays.size), self.n_qbins,
-                                   self.path, int(block_frames), ctypes.byref(h))
+        if n_slabs != 1:
+            if self.path != PATH_FUSED_F32 or block_frames:
+                raise ValueError("mode slabs run on the fused FP32 path with the default block")
+            rc = self._L.nfs_create_slab(self.H, self.W, _ptr(self.delays), int(self.delays.size), self.n_qbins,
+                                         int(slab), int(n_slabs), ctypes.byref(h))
+            what = "nfs_create_slab"
+        else:
+            rc = self._L.nfs_create_ex(self.H, self.W, _ptr(self.delays), int(self.delays.size), self.n_qbins,
+                                       self.path, int(block_frames), ctypes.byref(h))
+            what = "nfs_create_ex"
         if rc != NFS_OK:
-            raise NFSError(rc, "nfs_create_ex")
+            raise NFSError(rc, what)
         self._h = h
 
     # --------------------------------------------------------------- helpers
@@ -282,6 +297,41 @@ class NFS:
         d = None if D is None else np.ascontiguousarray(np.asarray(D, np.float64))
         self._check(self._L.nfs_fit(self._h, _ptr(d), _ptr(a), _ptr(b), _ptr(g), int(iters), int(method)), "nfs_fit")
         return a, b, g
+
+
+def slab_range(H: int, W: int, slab: int, n_slabs: int):
+    """(first mode, modes) of a slab in the column-major order k = k_x H + k_y (host logic)."""
+    L = load_library()
+    a, b = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = L.nfs_slab_range(int(H), int(W), int(slab), int(n_slabs), ctypes.byref(a), ctypes.byref(b))
+    if rc != NFS_OK:
+        raise NFSError(rc, "nfs_slab_range")
+    return a.value, b.value
+
+
+def reduce_slabs(results, group=None) -> dict:
+    """The whole result from the structure functions of the slabs of one frame sequence: D summed
+    (each slab's D is its share of every bin average); counts and q_mean are the slabs' common ones.
+
+    results: a list of per-slab dicts (slabs in one process), or, with a torch.distributed process
+    group, this rank's own dict: D is then summed over the group's ranks (one all-reduce of
+    n_delays x n_qbins doubles, in host memory: use a gloo group)."""
+    if group is None:
+        out = dict(results[0])
+        D = np.zeros_like(results[0]["D"])
+        for r in results:
+            assert np.array_equal(r["bin_counts"], out["bin_counts"]) and np.array_equal(r["pair_counts"],
+                                                                                          out["pair_counts"])
+            D = D + r["D"]
+        out["D"] = D
+        return out
+    import torch
+    import torch.distributed as dist
+    out = dict(results)
+    t = torch.from_numpy(np.ascontiguousarray(out["D"], dtype=np.float64).copy())
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    out["D"] = t.numpy()
+    return out
 
 
 def structure_function_noalloc(frames, delays, n_qbins: int, stream: int = 0) -> dict:

@@ -50,17 +50,23 @@ def _stale(target: str, deps) -> bool:
 SANITIZE_FLAGS = ["-Xcompiler", "-fsanitize=address,-fsanitize=undefined,-fno-omit-frame-pointer", "-g"]
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, sanitize: bool = False) -> str:
+# Cycle accounting of the fused delay kernel's warp roles (nfs_delay_profile): a measuring build.
+PROFILE_FLAGS = ["-DNFS_DELAY_PROFILE"]
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, sanitize: bool = False,
+          profile: bool = False) -> str:
     """Compile every translation unit and link the library; returns its path.  sanitize=True builds
-    a separate copy with AddressSanitizer and UBSan in the host code (loaded with libasan preloaded)."""
-    out = OUT + ("_sanitize" if sanitize else "")
+    a separate copy with AddressSanitizer and UBSan in the host code (loaded with libasan preloaded);
+    profile=True a separate copy whose delay kernel accounts its warps' clock cycles by phase."""
+    out = OUT + ("_sanitize" if sanitize else "") + ("_profile" if profile else "")
     lib = os.path.join(out, os.path.basename(LIB))
     os.makedirs(out, exist_ok=True)
     cc = nvcc()
     hdrs = _headers()
     jobs = []
     objs = []
-    extra = SANITIZE_FLAGS if sanitize else []
+    extra = (SANITIZE_FLAGS if sanitize else []) + (PROFILE_FLAGS if profile else [])
     for src in _sources():
         obj = os.path.join(out, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
@@ -82,7 +88,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, 
                 raise RuntimeError(f"nvcc failed for {cmd[-3]}")
     if force or jobs or _stale(lib, objs):
         tmp = lib + f".{os.getpid()}.tmp"
-        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", *extra[:2]]
+        cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static", *(SANITIZE_FLAGS[:2] if sanitize else [])]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode:
             raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

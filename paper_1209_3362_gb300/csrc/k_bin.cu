@@ -61,7 +61,8 @@ __global__ void k_export(const Acc *__restrict__ acc_j, Geometry g, long long pa
     const double inv = pairs > 0 ? 1.0 / (double)pairs : 0.0;
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
         const size_t ky = i / g.Wh, kx = i - ky * g.Wh;
-        out[i] = acc_value(acc_j, g.mode((int)kx, (int)ky)) * inv;
+        const size_t kl = g.mode((int)kx, (int)ky) - g.k0;  // modes outside a slab read as 0
+        out[i] = kl < g.M ? acc_value(acc_j, kl) * inv : 0.0;
     }
 }
 

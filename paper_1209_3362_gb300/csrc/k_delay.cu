@@ -178,6 +178,32 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// ------------------------------------------------------------------ cycle accounting (measuring build)
+
+// With NFS_DELAY_PROFILE defined (buildlib.build(profile=True)) the tiled kernel adds each warp
+// role's clock64 cycles by phase into g_delay_prof (lane 0 of each warp; read and cleared through
+// nfs_delay_profile); otherwise the accounting compiles to nothing.
+enum DelayProf {
+    kProfConsumer,      // consumer warps: from the first copy-group wait to the last hand-over
+    kProfConsWaitGroup, //   waiting for copy groups
+    kProfConsWaitFree,  //   waiting for a free partial-sum buffer
+    kProfConsCompute,   //   pair arithmetic of the sub-runs
+    kProfConsHand,      //   step and batch hand-overs
+    kProfWriter,        // writer warp: whole tile
+    kProfWriterWait,    //   waiting for written batches
+    kProfProducerWait,  // producer lane: waiting for free slot-ring rows
+    kProfPrologue,      // thread 0: barrier set-up to the first synchronisation
+    kProfEpilogue,      // thread 0: final synchronisation and barrier invalidation
+    kProfTiles,         // tile passes counted
+    kProfSlots
+};
+#ifdef NFS_DELAY_PROFILE
+__device__ unsigned long long g_delay_prof[kProfSlots];
+#define NFS_PROF(x) x
+#else
+#define NFS_PROF(x)
+#endif
+
 // ------------------------------------------------------------------ tiled kernel
 
 constexpr int kWarps = 16;                       // consumer warps (32 frames each: 16 per half-warp)
@@ -445,6 +471,7 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                                           size_t tile, const float2 *__restrict__ ring_cur = nullptr, int R_cur = 0)
 {
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    NFS_PROF(long long pf_t0 = clock64(); long long pf[kProfSlots] = {};)
 
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_init(&S.full[b], 1);
@@ -459,6 +486,7 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    NFS_PROF(if (tid == 0) pf[kProfPrologue] += clock64() - pf_t0;)
 
     if (warp == kProducer) {
         // issue every copy group as soon as its rows are free and its barrier is reusable
@@ -470,6 +498,7 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                 if (g == stall_group) break;
                 const int need = (g == 0) ? 0 : sched.st[g - 1].need;
                 bool ok = true;
+                NFS_PROF(const long long pw0 = clock64();)
                 if (min_steps(S) < need) {
                     const unsigned long long tw = global_ns();
                     const long long c0 = clock64();
@@ -489,6 +518,7 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                         __nanosleep(64);
                     }
                 }
+                NFS_PROF(pf[kProfProducerWait] += clock64() - pw0;)
                 if (!ok) break;
                 __threadfence_block();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -532,11 +562,14 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
             for (int q = 0; q < 8; ++q)
                 if (jh + q < n && (unsigned)(jb + jh + q) < (unsigned)nd) old[q] = base[(size_t)(jb + jh + q) * M];
         };
+        NFS_PROF(const long long pwr = clock64();)
         for (int k = 0; k < nbatch; ++k) {
             const int b = k % kRedBufs;
             // After a failed wait the batch may not be written yet: stop touching global memory
             // (the launch's results are void and the error word says so).
+            NFS_PROF(const long long pww = clock64();)
             if (!wait_bar(S, &S.red_full[b], (unsigned)((k / kRedBufs) & 1), err, 2, k)) break;
+            NFS_PROF(pf[kProfWriterWait] += clock64() - pww;)
             if (r < nsr) {
                 next_batch();
                 load_old();
@@ -560,13 +593,16 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                 *(volatile int *)&S.wdrained = k + 1;
             }
         }
+        NFS_PROF(pf[kProfWriter] += clock64() - pwr;)
     } else {
         // consumers
         const int taw = (int)(t0 + (long long)warp * 2 * kTw);  // first frame of this warp (indices < 2^31)
         const int ta = taw + (lane >> 4) * kTw;                 // first frame of this lane's half-warp
         const int hi_lim = (int)(t0 + nb - ta);                 // frames ta + i are new frames for i < hi_lim
         const int hi_lim_w = (int)(t0 + nb - taw);
+        NFS_PROF(const long long pc0 = clock64(); long long pq = pc0;)
         wait_group(S, 0, err);
+        NFS_PROF(pf[kProfConsWaitGroup] += clock64() - pq;)
         pk_t xt[kTw];
 #pragma unroll
         for (int i = 0; i < kTw; ++i)
@@ -583,25 +619,36 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         open_batch(0);
         for (int s = 0; s < nst; ++s) {
             const Stage st = sched.st[s];
+            NFS_PROF(pq = clock64();)
             wait_group(S, s + 1, err);
+            NFS_PROF(pf[kProfConsWaitGroup] += clock64() - pq;)
             for (int r = st.sr0; r < st.sr0 + st.nsr; ++r) {
                 const SubRun sr = sched.sr[r];
                 if (pend + sr.len > 16) {
+                    NFS_PROF(pq = clock64();)
                     hand_over(S, batch % kRedBufs, lane);
                     ++batch;
                     pend = 0;
+                    NFS_PROF(long long pq2 = clock64(); pf[kProfConsHand] += pq2 - pq;)
                     open_batch(batch);
+                    NFS_PROF(pf[kProfConsWaitFree] += clock64() - pq2;)
                 }
+                NFS_PROF(pq = clock64();)
                 subrun_dispatch<PACKED>(S, xt, lane, warp, taw, ta, sr.d0, sr.len, S.red[batch % kRedBufs], pend, hi_lim,
                                         hi_lim_w);
+                NFS_PROF(pf[kProfConsCompute] += clock64() - pq;)
                 pend += sr.len;
             }
+            NFS_PROF(pq = clock64();)
             step_done(S, lane);
+            NFS_PROF(pf[kProfConsHand] += clock64() - pq;)
         }
         if (pend) {
             hand_over(S, batch % kRedBufs, lane);
         }
+        NFS_PROF(pf[kProfConsumer] += clock64() - pc0;)
     }
+    NFS_PROF(const long long pe0 = clock64();)
     __syncthreads();  // every role has finished this tile (all copies issued were consumed)
     if (tid == 0) {
         for (int b = 0; b < kFullBars; ++b) mbar_inval(&S.full[b]);
@@ -611,6 +658,15 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         }
     }
     __syncthreads();
+#ifdef NFS_DELAY_PROFILE
+    if (tid == 0) {
+        pf[kProfEpilogue] += clock64() - pe0;
+        pf[kProfTiles] += 1;
+    }
+    if (lane == 0)
+        for (int q = 0; q < kProfSlots; ++q)
+            if (pf[q]) atomicAdd(&g_delay_prof[q], (unsigned long long)pf[q]);
+#endif
 }
 
 template <bool PACKED>
@@ -802,3 +858,25 @@ cudaError_t launch_delay_f64(const double2 *ring, int R, size_t M, long long t, 
 }
 
 }  // namespace nfs
+
+// The delay kernel's cycle accounting (a measuring build only): out[0 .. n) = the kProfSlots sums
+// (see DelayProf), cleared afterwards when reset != 0.
+extern "C" int nfs_delay_profile(unsigned long long *out, int n, int reset)
+{
+#ifdef NFS_DELAY_PROFILE
+    if (!out || n < 0) return NFS_EINVAL;
+    unsigned long long h[nfs::kProfSlots] = {};
+    if (cudaMemcpyFromSymbol(h, nfs::g_delay_prof, sizeof(h)) != cudaSuccess) return NFS_ECUDA;
+    for (int i = 0; i < n && i < nfs::kProfSlots; ++i) out[i] = h[i];
+    if (reset) {
+        const unsigned long long z[nfs::kProfSlots] = {};
+        if (cudaMemcpyToSymbol(nfs::g_delay_prof, z, sizeof(z)) != cudaSuccess) return NFS_ECUDA;
+    }
+    return nfs::kProfSlots;
+#else
+    (void)out;
+    (void)n;
+    (void)reset;
+    return NFS_EUNSUPPORTED;
+#endif
+}

@@ -224,7 +224,7 @@ __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
     C *bufA = reinterpret_cast<C *>(smem_raw);
     C *bufB = bufA + (size_t)H * CB;
     const int f = blockIdx.y;
-    const int x0 = blockIdx.x * CB;
+    const int x0 = blockIdx.x * CB + 2 * g.kp0;
     const int slot = (slot0 + f) % R;
     const C *src = scratch + (size_t)f * g.H * g.Wp;
     for (int e = threadIdx.x; e < H * CB; e += blockDim.x) {
@@ -240,7 +240,8 @@ __global__ void __launch_bounds__(256) k_col_fft(Geometry g, FftPlan plan,
         const int y = e / CB, c = e - y * CB;
         const int x = x0 + c;
         if (sizeof(T) == 4) {
-            if (x < g.Wh) ring[ring_index(slot, g.mode(x, y), R)] = Y[e];
+            const size_t kl = g.mode(x, y) - g.k0;  // the slab's modes only (wraps above M below k0)
+            if (x < g.Wh && kl < g.M) ring[ring_index(slot, kl, R)] = Y[e];
         } else if (x < g.Wp) {
             ring[(size_t)slot * g.M + (size_t)y * g.Wp + x] = Y[e];
         }
@@ -311,7 +312,7 @@ cudaError_t launch_col_fft(int nf, const Geometry &g, const FftPlan &plan, const
         cudaError_t e = cudaFuncSetAttribute(k_col_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((g.Wp + cb - 1) / cb, nf);
+    dim3 grid(sizeof(T) == 4 ? (unsigned)((2 * g.ncp + cb - 1) / cb) : (unsigned)((g.Wp + cb - 1) / cb), nf);
     k_col_fft<T><<<grid, 256, smem, s>>>(g, plan, tw_col, ring, R, slot0, cb, scratch);
     return cudaGetLastError();
 }
@@ -339,7 +340,26 @@ Geometry make_geometry(int H, int W, bool colmajor)
     g.colmajor = colmajor ? 1 : 0;
     const size_t m = colmajor ? (size_t)g.Wh * H : (size_t)H * g.Wp;
     g.M = (m + kTile - 1) / kTile * kTile;
+    g.k0 = 0;
+    g.kp0 = 0;
+    g.ncp = g.Wp / 2;
     return g;
+}
+
+bool make_slab(Geometry *g, int slab, int n_slabs)
+{
+    if (!g->colmajor || g->k0 != 0) return false;
+    const long long T = (long long)(g->M / kTile);
+    if (n_slabs < 1 || slab < 0 || slab >= n_slabs || n_slabs > T) return false;
+    const long long tb = T * slab / n_slabs, te = T * (slab + 1) / n_slabs;
+    g->k0 = (size_t)tb * kTile;
+    g->M = (size_t)(te - tb) * kTile;
+    const long long c0 = (long long)(g->k0 / (size_t)g->H);
+    long long c1 = (long long)((g->k0 + g->M - 1) / (size_t)g->H);
+    if (c1 > g->Wh - 1) c1 = g->Wh - 1;  // the last tile's padding modes belong to no column
+    g->kp0 = (int)(c0 / 2);
+    g->ncp = (int)(c1 / 2 - c0 / 2 + 1);
+    return true;
 }
 
 bool make_plan(int L, FftPlan *plan)

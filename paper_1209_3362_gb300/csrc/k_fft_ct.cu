@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(col_threads(H)) k_col_fft_ct(Geometry g, const
     static_assert(N % NT == 0, "column batch must fill the CTA");
     __shared__ __align__(16) float2 buf[padded(N)];
     const int f = blockIdx.y;
-    const int kp = blockIdx.x;
+    const int kp = blockIdx.x + g.kp0;
     const int slot = (slot0 + f) % R;
     const float2 *src = scratch + (size_t)f * H * g.Wp + (size_t)kp * H * 2;
 #pragma unroll
@@ -359,7 +359,8 @@ __global__ void __launch_bounds__(col_threads(H)) k_col_fft_ct(Geometry g, const
         const int e = threadIdx.x + p * NT;
         const int c = e / H, y = e % H;
         const int kx = 2 * kp + c;
-        if (kx < g.Wh) ring[ring_index(slot, (size_t)kx * H + y, R)] = Y[padded(y * 2 + c)];
+        const size_t kl = (size_t)kx * H + y - g.k0;  // the slab's modes only
+        if (kx < g.Wh && kl < g.M) ring[ring_index(slot, kl, R)] = Y[padded(y * 2 + c)];
     }
 }
 
@@ -396,7 +397,7 @@ template <int H>
 static cudaError_t col_ct(int nf, const Geometry &g, const float2 *tws, const float2 *scratch, float2 *ring, int R,
                           int slot0, cudaStream_t s)
 {
-    dim3 grid(g.Wp / 2, nf);
+    dim3 grid(g.ncp, nf);
     ct::k_col_fft_ct<H><<<grid, ct::col_threads(H), 0, s>>>(g, tws, scratch, ring, R, slot0);
     return cudaGetLastError();
 }

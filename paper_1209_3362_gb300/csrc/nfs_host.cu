@@ -173,8 +173,10 @@ int build_bins(nfs_ctx *c)
         for (int kx = 0; kx < Wh; ++kx) {
             const int b = bin_of[(size_t)ky * Wh + kx];
             if (b < 0) continue;
+            const long long kl = (long long)c->g.mode(kx, ky) - (long long)c->g.k0;  // slab-local index
+            if (kl < 0 || kl >= (long long)c->g.M) continue;
             const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
-            lists[b].push_back((int)(((long long)c->g.mode(kx, ky) << 1) | two));
+            lists[b].push_back((int)((kl << 1) | two));
         }
     std::vector<int> off((size_t)nq + 1, 0), modes;
     for (int b = 0; b < nq; ++b) off[b + 1] = off[b] + (int)lists[b].size();
@@ -434,10 +436,11 @@ int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, i
 }
 
 int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
-                bool cross)
+                bool cross, int slab, int n_slabs)
 {
     if (!out) return NFS_EINVAL;
     if (cross && path != NFS_PATH_FUSED_F32) return NFS_EINVAL;
+    if (n_slabs != 1 && (path != NFS_PATH_FUSED_F32 || cross)) return NFS_EINVAL;
     *out = nullptr;
     const int rc_args = check_args(H, W, delays, n_delays, n_qbins, path, block);
     if (rc_args) return rc_args;
@@ -453,6 +456,12 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     c->delays.assign(delays, delays + n_delays);
     c->tau_max = delays[n_delays - 1];
     c->g = make_geometry(H, W, c->f32());
+    c->slab = slab;
+    c->n_slabs = n_slabs;
+    if (n_slabs != 1 && !make_slab(&c->g, slab, n_slabs)) {
+        delete c;
+        return NFS_EINVAL;
+    }
     c->R = c->tau_max + (c->f32() ? c->K : kMaxChunk);
     c->stage_frames = (int)std::max<size_t>(
         1, std::min<size_t>(c->f32() ? kMaxChunkF32 : kMaxChunk, (64u << 20) / c->frame_bytes()));
@@ -560,6 +569,27 @@ int nfs_create_ex(int H, int W, const int32_t *delays, int n_delays, int n_qbins
                   nfs_ctx **out)
 {
     return create_impl(H, W, delays, n_delays, n_qbins, path, block_frames, out);
+}
+
+int nfs_create_slab(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int slab, int n_slabs,
+                    nfs_ctx **out)
+{
+    if (!out) return NFS_EINVAL;
+    *out = nullptr;
+    if (n_slabs < 1 || slab < 0 || slab >= n_slabs) return NFS_EINVAL;
+    return create_impl(H, W, delays, n_delays, n_qbins, NFS_PATH_FUSED_F32, 0, out, false, slab, n_slabs);
+}
+
+int nfs_slab_range(int H, int W, int slab, int n_slabs, int64_t *first_mode, int64_t *n_modes)
+{
+    if (!first_mode || !n_modes) return NFS_EINVAL;
+    if (H < 2 || W < 2 || H > kMaxDim || W > kMaxDim || (H % 2) || (W % 2) || !factors_2_3(H) || !factors_2_3(W / 2))
+        return NFS_EUNSUPPORTED;
+    Geometry g = make_geometry(H, W, true);
+    if (!make_slab(&g, slab, n_slabs)) return NFS_EINVAL;
+    *first_mode = (int64_t)g.k0;
+    *n_modes = (int64_t)g.M;
+    return NFS_OK;
 }
 
 int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_counts, double *q_mean)
@@ -817,6 +847,8 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_DELAY_VARIANT: *v = c->delay_variant; return NFS_OK;
         case NFS_OPT_FFT_GENERIC: *v = c->fft_generic; return NFS_OK;
         case NFS_OPT_TEST_STALL_GROUP: *v = c->stall_group; return NFS_OK;
+        case NFS_OPT_SLAB_FIRST_MODE: *v = (int64_t)c->g.k0; return NFS_OK;
+        case NFS_OPT_SLAB_MODES: *v = (int64_t)c->g.M; return NFS_OK;
         default: return NFS_EINVAL;
     }
 }

@@ -96,6 +96,7 @@ struct nfs_ctx {
     // the old sequence's to d_ring.  Both sequences advance together: frame u of each per step.
     bool cross = false;
     void *d_ring_cur = nullptr;
+    int slab = 0, n_slabs = 1;  // mode slab of this context (g.k0, g.M); 0 of 1 = the whole spectrum
     long long transforms = 0;  // frames transformed (both sequences of a cross pass)
 
     std::vector<long long> counts, pairs_h;
@@ -170,7 +171,7 @@ int next_chunk(const nfs_ctx *c, long long remaining, int cap);
 int enter(nfs_ctx *c);
 int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block);
 int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
-                bool cross = false);
+                bool cross = false, int slab = 0, int n_slabs = 1);
 bool is_page_locked(const void *p);
 
 }  // namespace host

@@ -45,9 +45,14 @@ struct Geometry {
     int Lr;        // row transform length W/2
     int Wh;        // W/2 + 1 non-redundant columns
     int Wp;        // W/2 + 1 rounded up to a multiple of 4 (row pitch / scratch columns)
-    size_t M;      // complex values per spectrum (multiple of 32)
+    size_t M;      // complex values per spectrum held (multiple of 16; a slab's share, see k0)
     size_t HW;     // pixels per frame
     int colmajor;  // 1: column-major mode order (FP32), 0: row-major with pitch Wp (FP64)
+    // Mode slab (FP32 path): the spectrum ring and accumulators hold modes k0 .. k0+M-1 of the
+    // column-major order, at local index k - k0; the column pass transforms column pairs
+    // kp0 .. kp0+ncp-1 only.  The whole spectrum: k0 = 0, kp0 = 0, ncp = Wp/2.
+    size_t k0;
+    int kp0, ncp;
     __host__ __device__ size_t mode(int kx, int ky) const
     {
         return colmajor ? (size_t)kx * H + ky : (size_t)ky * Wp + kx;
@@ -58,6 +63,9 @@ struct Geometry {
     }
 };
 Geometry make_geometry(int H, int W, bool colmajor);
+// Slab `slab` of n_slabs of the FP32 geometry g (its 16-mode tiles split evenly, in order): sets k0,
+// M, kp0 and ncp.  False if n_slabs < 1, slab out of range or more slabs than tiles.
+bool make_slab(Geometry *g, int slab, int n_slabs);
 
 // --------------------------------------------------------------- launchers (stream-ordered)
 

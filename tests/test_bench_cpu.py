@@ -29,3 +29,27 @@ def test_block_bytes_brute_force():
         want += 8 * M * len(slots) + 16 * M * len(active)
     assert (total, launches, pairs) == (want, 3, want_pairs)
     assert pairs == sum(max(0, N - d) for d in delays)
+
+
+def test_oracle_sample_takes_the_jobs_own_delay_prefix():
+    """The timed oracle samples (reference arm and cpu_baseline leg) use the job's first n frames
+    and the job's own delays below n, with at most the target number of pairs."""
+    w = S.WORKLOADS["ddm2048"]
+    n, delays, pairs = bench.sample_shape(w.delays, 100, 64)
+    assert delays == [d for d in w.delays if d < n] and pairs == sum(n - d for d in delays) <= 100
+    n2, _, pairs2 = bench.sample_shape(w.delays, 101 + pairs, 64)
+    assert n2 > n and pairs2 > pairs
+    n3, d3, _ = bench.sample_shape(S.WORKLOADS["paper512"].delays, 10 ** 9, 40)
+    assert n3 == 40 and d3 == list(range(1, 40))
+
+
+def test_reference_arm_prints_its_line():
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--workload", "ddm128", "--steps", "2",
+                          "--warmup", "1", "--ref-budget", "0.3"], capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "ddm128"

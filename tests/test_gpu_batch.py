@@ -69,3 +69,33 @@ def test_batch_device_push_all_at_once(ragged):
     for s in range(len(shapes)):
         assert rel_err(got[s], refs[s]) <= TOL_F32, s
         assert got2[s]["pair_counts"].max() <= 99
+
+
+@pytest.fixture(scope="module")
+def camera_shapes(oracle_lib):
+    """The ragged workload's six camera shapes (128^2 .. 1024^2, radix-3 ones included), 520 frames
+    each so that every member completes a 512-frame block and the persistent batched delay kernel
+    runs over the large members' tiles, 12 log delays 1..260 and n_q = min(H, W) / 2."""
+    P.build()
+    shapes = [(1024, 1024), (768, 1024), (384, 512), (512, 512), (256, 256), (128, 128)]
+    delays = [S.log_delays(1, 260, 12)] * len(shapes)
+    nqs = [min(h, w) // 2 for h, w in shapes]
+    frames = [S.OUFrameSource(h, w, 0.3 + 0.9 * i, seed=700 + i).frames_numpy(520) for i, (h, w) in enumerate(shapes)]
+    refs = [oracle_lib.structure_function(f, d, q) for f, d, q in zip(frames, delays, nqs)]
+    return shapes, delays, nqs, frames, refs
+
+
+def test_batch_of_camera_shapes_matches_oracle(camera_shapes):
+    shapes, delays, nqs, frames, refs = camera_shapes
+    dev = [torch.from_numpy(f.view(np.int16)).cuda() for f in frames]
+    with P.NFSBatch(shapes, delays, nqs) as b:
+        b.push_frames_device(dev)
+        got = [b.structure_function(s) for s in range(len(shapes))]
+    for s in range(len(shapes)):
+        np.testing.assert_array_equal(got[s]["bin_counts"], refs[s]["bin_counts"])
+        np.testing.assert_array_equal(got[s]["pair_counts"], refs[s]["pair_counts"])
+        assert rel_err(got[s], refs[s]) <= TOL_F32, (shapes[s], rel_err(got[s], refs[s]))
+        with P.NFS(shapes[s][0], shapes[s][1], delays[s], nqs[s]) as ctx:
+            ctx.push_frames_device(dev[s])
+            single = ctx.structure_function()
+        np.testing.assert_array_equal(got[s]["D"], single["D"])
