@@ -322,12 +322,21 @@ def main():
     del src
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    # the pinned host copy for the end-to-end run, allocated and filled before the library's own
-    # allocations (as an acquisition program would hold its frame buffer)
+    # the pinned host copy for the end-to-end run, allocated before the library's own allocations
+    # and written by the CPU (as an acquisition program holds its frame buffer and writes frames
+    # into it): the frames pass through a small page-locked staging buffer.  (On some boxes a large
+    # page-locked buffer written only by the GPU's copy engines was read back 10-20x slower for
+    # its first few GB; see the end-to-end notes of the design.)
     host = None
     if not args.no_e2e:
         host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
-        host.copy_(frames)
+        stg = torch.empty((64, w.H, w.W), dtype=torch.int16, pin_memory=True)
+        for o in range(0, w.N, 64):
+            n = min(64, w.N - o)
+            stg[:n].copy_(frames[o:o + n])
+            torch.cuda.synchronize()
+            host[o:o + n].copy_(stg[:n])
+        del stg
 
     if slabs:
         ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, slab=rank, n_slabs=world)

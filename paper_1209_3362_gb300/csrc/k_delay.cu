@@ -209,8 +209,9 @@ __device__ unsigned long long g_delay_prof[kProfSlots];
 constexpr int kWarps = 16;                       // consumer warps (32 frames each: 16 per half-warp)
 constexpr int kTw = 16;                          // consecutive frames per lane (a half-warp's run)
 constexpr int kProducer = kWarps;                // warp that issues the copy groups
-constexpr int kWriter = kWarps + 1;              // warp that reduces partial sums into the accumulators
-constexpr int kThreads = (kWarps + 2) * 32;
+constexpr int kWriter = kWarps + 1;              // first of the warps that reduce partial sums into the
+constexpr int kWriters = 2;                      // accumulators (writer i takes the batches k = i mod 2)
+constexpr int kThreads = (kWarps + 1 + kWriters) * 32;
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
 static_assert(kWarps * 2 * kTw == kDelayBlock, "block = warps x half-warps x frames per lane");
 static_assert(kTile == 16, "a half-warp covers one tile: lane = mode + 16 x half");
@@ -229,7 +230,7 @@ struct TiledSmem {
     int wsteps[kWarps];                    // per consumer warp: steps completed (the producer waits for
                                            // the minimum: a sum would let fast warps count for a slow one)
     int wbatches[kWarps];                  // per consumer warp: batches handed over (diagnostics)
-    int wdrained;                          // batches the writer has drained (diagnostics)
+    int wdrained;                          // batches the writers have drained (diagnostics)
 };
 
 // err[0] = 1 once any wait of the launch gives up; the first thread to give up records in err[1..]
@@ -540,13 +541,17 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
                 }
             }
         }
-    } else if (warp == kWriter) {
+    } else if (warp >= kWriter) {
         // Reduce each batch over the consumer warps in a fixed order and add it to the Kahan pairs.
         // A batch is the longest run of consecutive sub-runs with at most 16 delays (the consumers'
-        // rule), so the writer takes every batch's delays from the schedule.  (Loading the next
-        // batch's accumulators right after releasing a buffer measured slower on runs of
+        // rule), so the writers take every batch's delays from the schedule; writer wi handles the
+        // batches k = wi mod kWriters (different delays: no two writers touch one accumulator).  A
+        // writer waits for batch k only after its batch k - kWriters, so every batch before k - 1
+        // is written and the buffer's mbarrier is in batch k's phase (no parity aliasing).  (Loading
+        // the next batch's accumulators right after releasing a buffer measured slower on runs of
         // consecutive delays than loading them once the batch is written.)
         // lane = mode + 16 h: half h adds the batch's delays 8 h .. 8 h + 7 at its mode.
+        const int wi = warp - kWriter;
         const int m = lane & (kTile - 1), jh = (lane >> 4) * 8;
         float2 *const base = acc + tile * kTile + m;
         const int nsr = nst > 0 ? sched.st[nst - 1].sr0 + sched.st[nst - 1].nsr : 0;
@@ -565,15 +570,14 @@ __device__ __forceinline__ void tile_pass(TiledSmem &S, const float2 *__restrict
         NFS_PROF(const long long pwr = clock64();)
         for (int k = 0; k < nbatch; ++k) {
             const int b = k % kRedBufs;
+            if (r < nsr) next_batch();
+            if (k % kWriters != wi) continue;
             // After a failed wait the batch may not be written yet: stop touching global memory
             // (the launch's results are void and the error word says so).
             NFS_PROF(const long long pww = clock64();)
             if (!wait_bar(S, &S.red_full[b], (unsigned)((k / kRedBufs) & 1), err, 2, k)) break;
             NFS_PROF(pf[kProfWriterWait] += clock64() - pww;)
-            if (r < nsr) {
-                next_batch();
-                load_old();
-            }
+            load_old();
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 if (jh + q < n && (unsigned)(jb + jh + q) < (unsigned)nd) {

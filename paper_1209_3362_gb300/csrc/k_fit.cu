@@ -82,14 +82,23 @@ __global__ void k_fit_gauss_newton(const float *__restrict__ D, const float *__r
     float a = A[b], bb = B[b], g = G[b];
     float lam = lambda0;
     float cur = bin_loss(D, tau, nd, nq, b, a, bb, g);
+    // The normal equations are formed in scaled units: residuals divided by the bin's largest |D|
+    // and each parameter's column multiplied by that parameter's current magnitude (Jacobi
+    // scaling), so that A ~ 1e8 next to B ~ 1e2 and Gamma ~ 1e-2 still gives an FP32-solvable
+    // 3x3 system; the step is scaled back afterwards.
+    float dmax = 0.f;
+    for (int j = 0; j < nd; ++j) dmax = fmaxf(dmax, fabsf(D[(size_t)j * nq + b]));
+    const float rs = dmax > 0.f ? 1.f / dmax : 1.f;
     for (int it = 0; it < iters; ++it) {
+        const float c[3] = {fmaxf(fabsf(a), 1e-6f * dmax + 1e-30f), fmaxf(fabsf(bb), 1e-6f * dmax + 1e-30f),
+                            fmaxf(fabsf(g), 1e-12f)};
         float M[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
         float v[3] = {0.f, 0.f, 0.f};
         for (int j = 0; j < nd; ++j) {
             const float t = __ldg(tau + j);
             const float e = expf(-g * t);
-            const float r = 2.f * a * (1.f - e) + 2.f * bb - D[(size_t)j * nq + b];
-            const float J[3] = {2.f * (1.f - e), 2.f, 2.f * a * t * e};
+            const float r = (2.f * a * (1.f - e) + 2.f * bb - D[(size_t)j * nq + b]) * rs;
+            const float J[3] = {2.f * (1.f - e) * c[0] * rs, 2.f * c[1] * rs, 2.f * a * t * e * c[2] * rs};
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
                 v[p] = fmaf(J[p], r, v[p]);
@@ -108,8 +117,8 @@ __global__ void k_fit_gauss_newton(const float *__restrict__ D, const float *__r
             const float rhs[3] = {-v[0], -v[1], -v[2]};
             float x[3];
             if (solve3(Md, rhs, x)) {
-                const float na = fmaxf(a + x[0], 0.f), nb = fmaxf(bb + x[1], 0.f);
-                const float ng = fmaxf(g + x[2], 1e-12f);
+                const float na = fmaxf(a + x[0] * c[0], 0.f), nb = fmaxf(bb + x[1] * c[1], 0.f);
+                const float ng = fmaxf(g + x[2] * c[2], 1e-12f);
                 const float nl = bin_loss(D, tau, nd, nq, b, na, nb, ng);
                 if (nl <= cur) {
                     a = na;
