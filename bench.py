@@ -258,6 +258,7 @@ def main():
     ap.add_argument("--delays", type=int, default=0, help="use delays 1..n (profiling cases; not a bench value)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--delay-variant", type=int, default=0, help="fused delay kernel variant (0 = default)")
+    ap.add_argument("--span", type=int, default=0, help="delay-kernel stage span (0 = choose by measurement)")
     ap.add_argument("--replicas", action="store_true", help="N > 1: independent sequences per rank (weak scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
@@ -344,7 +345,10 @@ def main():
         ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, path="f32", block_frames=args.block)
     if args.delay_variant:
         ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
+    if not args.delay_variant:
+        ctx.set_option(P.OPT_DELAY_SPAN, args.span)  # 0: measured on this delay list (results do not change)
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
+    ctx_span = ctx.get_option(P.OPT_DELAY_SPAN)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
@@ -510,6 +514,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
+                           "delay_span": ctx_span,
                            "parallelism": (f"mode-slabs{world}" if slabs else f"replicas{world}"),
                            "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "

@@ -128,9 +128,12 @@ int nfs_push_frames(nfs_ctx *ctx, const uint16_t *host_frames, int n_frames);
 
 /*
  * Append n_frames frames already in DEVICE memory of the context's device (same layout as
- * nfs_push_frames).  The buffer must stay valid and unchanged until the context's stream has
- * passed the work (nfs_synchronize() or any call that returns results).  The address must be
- * 2-byte aligned; 16-byte alignment with W a multiple of 8 takes the vectorised loads.
+ * nfs_push_frames).  The call enqueues the reads on the context's stream (nfs_get_stream) and
+ * returns: the frames must be completely written before that stream reaches them (finish the
+ * writing work first, or make that stream wait for it, e.g. cudaStreamWaitEvent), and the buffer
+ * must stay valid and unchanged until the context's stream has passed the work
+ * (nfs_synchronize() or any call that returns results).  The address must be 2-byte aligned;
+ * 16-byte alignment with W a multiple of 8 takes the vectorised loads.
  */
 int nfs_push_frames_device(nfs_ctx *ctx, const uint16_t *dev_frames, int n_frames);
 
@@ -193,6 +196,13 @@ void *nfs_get_stream(const nfs_ctx *ctx);
                                       stops issuing copies from this group on, so a consumer's bounded
                                       wait runs out (~2 s) and the call returns NFS_ETIMEOUT; checks
                                       the failure path without faulting the GPU */
+#define NFS_OPT_DELAY_SPAN 12   /* fused delay kernel: widest delay range of one copy stage, 16..512
+                                   (default 240); 0 = choose by measurement among 112, 176, 240,
+                                   320 and 400 on this context's own delay list (FP32 path, only
+                                   before the first frame: the measurement runs the kernel on the
+                                   ring and clears the accumulators afterwards, NFS_ESTATE once frames
+                                   were pushed).  The span regroups copy stages only: results are
+                                   bit-identical for every span */
 #define NFS_OPT_SLAB_FIRST_MODE 10 /* read-only: first mode (column-major order) of a slab context */
 #define NFS_OPT_SLAB_MODES 11      /* read-only: modes held (the slab's share, a multiple of 16) */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);
@@ -389,11 +399,14 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
  *                t0 - (largest delay) .. t0 + block_frames - 1 - (smallest delay)
  *   n_subruns, n_stages, block_frames, slot_rows, copy_barriers   out (copy group g waits on
  *                barrier g mod copy_barriers; the last three may be NULL)
+ *   span         widest delay range of one stage, 16 .. 512 (0 = the default 240; see
+ *                NFS_OPT_DELAY_SPAN)
  * NFS_ETOOBIG if an array would need more than max_entries entries (the counts are still set).
+ * NFS_EINVAL also for a span outside 16 .. 512.
  */
 int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *subruns, int32_t *stages,
                        int max_entries, int *n_subruns, int *n_stages, int *block_frames, int *slot_rows,
-                       int *copy_barriers);
+                       int *copy_barriers, int span);
 
 /*
  * ---------------------------------------------------------------- analysis without allocation

@@ -40,6 +40,7 @@ OPT_FFT_GENERIC = 8
 OPT_TEST_STALL_GROUP = 9
 OPT_SLAB_FIRST_MODE = 10
 OPT_SLAB_MODES = 11
+OPT_DELAY_SPAN = 12
 FIT_GAUSS_NEWTON = 0
 FIT_ADAM = 1
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
@@ -95,7 +96,7 @@ def load_library(path: Optional[str] = None):
         "nfs_structure_function_noalloc": (I, [V, I, I, I, V, I, I, V, V, V, V]),
         "nfs_out_of_core_plan": (I, [V, I, I64, I64, V, V, ctypes.POINTER(I), ctypes.POINTER(I64)]),
         "nfs_delay_schedule": (I, [V, I, I, V, V, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I),
-                                   ctypes.POINTER(I), ctypes.POINTER(I)]),
+                                   ctypes.POINTER(I), ctypes.POINTER(I), I]),
         "nfs_structure_function_out_of_core": (I, [I, I, V, I, I, V, I64, I64, V, V, V, V, ctypes.POINTER(I64)]),
         "nfs_fit": (I, [V, V, V, V, V, I, I]),
         "nfs_batch_create": (I, [I, V, V, V, V, V, PP]),
@@ -145,6 +146,36 @@ def _ptr(a):
     return ctypes.c_void_p(a.ctypes.data) if a is not None else None
 
 
+def _after_current_stream(stream_handle: int, device):
+    """Make the library's stream wait for the work queued so far on PyTorch's current stream (which
+    may still be writing the frames about to be pushed)."""
+    import torch
+    ev = torch.cuda.Event()
+    ev.record(torch.cuda.current_stream(device))
+    torch.cuda.ExternalStream(stream_handle, device=device).wait_event(ev)
+
+
+class _InFlight:
+    """Device tensors the library may still be reading on its own stream, each with an event
+    recorded on that stream after its push: the tensors stay referenced (so PyTorch's caching
+    allocator cannot hand their memory to other tensors) until their events have completed; entries
+    are dropped as they complete and all at once after calls that synchronise the stream.  (The C
+    ABI requires device frames to stay valid until the context's stream has passed them.)"""
+
+    def __init__(self):
+        self.items = []
+
+    def add(self, tensor, stream_handle: int):
+        import torch
+        ev = torch.cuda.Event()
+        ev.record(torch.cuda.ExternalStream(stream_handle, device=tensor.device))
+        self.items = [(t, e) for (t, e) in self.items if not e.query()]
+        self.items.append((tensor, ev))
+
+    def clear(self):
+        self.items = []
+
+
 class NFS:
     """One analysis context: frames in, binned structure function D_b(tau) out (Eq. 1, Fig. 1e,f)."""
 
@@ -171,6 +202,7 @@ class NFS:
         if rc != NFS_OK:
             raise NFSError(rc, what)
         self._h = h
+        self._inflight = _InFlight()
 
     # --------------------------------------------------------------- helpers
     def _check(self, rc: int, what: str):
@@ -184,8 +216,10 @@ class NFS:
 
     def close(self):
         if getattr(self, "_h", None):
-            self._L.nfs_destroy(self._h)
+            self._L.nfs_destroy(self._h)  # synchronises the context's streams first
             self._h = None
+        if getattr(self, "_inflight", None):
+            self._inflight.clear()
 
     def __del__(self):
         try:
@@ -215,11 +249,18 @@ class NFS:
         self._check(self._L.nfs_push_frames(self._h, _ptr(a), a.shape[0]), "nfs_push_frames")
 
     def push_frames_device(self, frames) -> None:
-        """Device frames: a CUDA torch tensor [n, H, W] of 2-byte integers (int16 storage of counts)."""
+        """Device frames: a CUDA torch tensor [n, H, W] of 2-byte integers (int16 storage of counts).
+
+        The library reads them asynchronously on its own stream: that stream first waits for the
+        work already queued on PyTorch's current stream (which may still be writing the frames), and
+        the context keeps the tensor referenced until its stream has read it, so PyTorch does not
+        hand its memory to other tensors even if the caller drops it at once."""
         assert frames.is_cuda and frames.is_contiguous() and frames.element_size() == 2
         n = frames.shape[0] if frames.dim() == 3 else 1
+        _after_current_stream(self.stream, frames.device)
         self._check(self._L.nfs_push_frames_device(self._h, ctypes.c_void_p(frames.data_ptr()), n),
                     "nfs_push_frames_device")
+        self._inflight.add(frames, self.stream)
 
     def push_frames_device_ptr(self, ptr: int, n: int) -> None:
         self._check(self._L.nfs_push_frames_device(self._h, ctypes.c_void_p(ptr), int(n)), "nfs_push_frames_device")
@@ -233,6 +274,7 @@ class NFS:
         qm = np.zeros(nq, np.float64)
         self._check(self._L.nfs_structure_function(self._h, _ptr(D), _ptr(bc), _ptr(pc), _ptr(qm)),
                     "nfs_structure_function")
+        self._inflight.clear()  # the call synchronised the stream
         return dict(D=D, bin_counts=bc, pair_counts=pc, q_mean=qm)
 
     def export_spectrum(self, j: int) -> np.ndarray:
@@ -245,6 +287,7 @@ class NFS:
 
     def synchronize(self):
         self._check(self._L.nfs_synchronize(self._h), "nfs_synchronize")
+        self._inflight.clear()
 
     @property
     def frame_count(self) -> int:
@@ -386,8 +429,9 @@ def out_of_core_plan(delays, n_frames: int, max_ring_slots: int) -> dict:
     return dict(band_first=first[:n + 1].copy(), band_shift=shift[:n].copy(), n_transforms=nt.value)
 
 
-def delay_schedule(delays, cross: bool = False) -> dict:
-    """The fused delay kernel's copy schedule for a delay list (host logic; see nfs_delay_schedule)."""
+def delay_schedule(delays, cross: bool = False, span: int = 0) -> dict:
+    """The fused delay kernel's copy schedule for a delay list (host logic; see nfs_delay_schedule;
+    span 0 = the default)."""
     L = load_library()
     d = np.ascontiguousarray(np.asarray(delays, dtype=np.int32))
     cap = max(16, d.size)
@@ -395,7 +439,7 @@ def delay_schedule(delays, cross: bool = False) -> dict:
     st = np.zeros((cap, 5), np.int32)
     out = [ctypes.c_int(0) for _ in range(5)]
     rc = L.nfs_delay_schedule(_ptr(d), int(d.size), int(bool(cross)), _ptr(sr), _ptr(st), cap,
-                              *[ctypes.byref(o) for o in out])
+                              *[ctypes.byref(o) for o in out], int(span))
     if rc != NFS_OK:
         raise NFSError(rc, "nfs_delay_schedule")
     nsr, nst, K, rows, bars = (o.value for o in out)
@@ -445,6 +489,7 @@ class NFSBatch:
         if rc != NFS_OK:
             raise NFSError(rc, "nfs_batch_create")
         self._h = h
+        self._inflight = _InFlight()
 
     def _check(self, rc, what):
         if rc != NFS_OK:
@@ -454,6 +499,8 @@ class NFSBatch:
         if getattr(self, "_h", None):
             self._L.nfs_batch_destroy(self._h)
             self._h = None
+        if getattr(self, "_inflight", None):
+            self._inflight.clear()
 
     def __del__(self):
         try:
@@ -476,7 +523,13 @@ class NFSBatch:
         n = len(self.shapes)
         ptrs = (ctypes.c_void_p * n)(*[(t.data_ptr() if t is not None else None) for t in tensors])
         counts = np.array([(t.shape[0] if t is not None else 0) for t in tensors], np.int32)
+        dev = next((t.device for t in tensors if t is not None), None)
+        if dev is not None:
+            _after_current_stream(self.stream, dev)
         self._check(self._L.nfs_batch_push_device(self._h, ptrs, _ptr(counts)), "nfs_batch_push_device")
+        for t in tensors:
+            if t is not None:
+                self._inflight.add(t, self.stream)
 
     def structure_function(self, seq):
         nd, nq = self.delays[seq].size, self.n_qbins[seq]
@@ -486,6 +539,7 @@ class NFSBatch:
         qm = np.zeros(nq, np.float64)
         self._check(self._L.nfs_batch_structure_function(self._h, int(seq), _ptr(D), _ptr(bc), _ptr(pc), _ptr(qm)),
                     "nfs_batch_structure_function")
+        self._inflight.clear()  # the call synchronised the batch's stream
         return dict(D=D, bin_counts=bc, pair_counts=pc, q_mean=qm)
 
     def reset(self):
@@ -493,6 +547,7 @@ class NFSBatch:
 
     def synchronize(self):
         self._check(self._L.nfs_batch_synchronize(self._h), "nfs_batch_synchronize")
+        self._inflight.clear()
 
     @property
     def stream(self) -> int:
@@ -533,6 +588,7 @@ class NFSRoi(NFSBatch):
         if rc != NFS_OK:
             raise NFSError(rc, "nfs_roi_create")
         self._h = hdl
+        self._inflight = _InFlight()
 
     def push_frames(self, frames):
         """frames: [n, H, W] full frames in host memory."""
@@ -543,5 +599,7 @@ class NFSRoi(NFSBatch):
     def push_frames_device(self, frames):
         """frames: CUDA tensor [n, H, W] of 2-byte integers (full frames)."""
         assert tuple(frames.shape[1:]) == (self.H, self.W) and frames.is_contiguous()
+        _after_current_stream(self.stream, frames.device)
         self._check(self._L.nfs_roi_push_device(self._h, ctypes.c_void_p(frames.data_ptr()), frames.shape[0]),
                     "nfs_roi_push_device")
+        self._inflight.add(frames, self.stream)

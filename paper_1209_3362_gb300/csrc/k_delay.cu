@@ -39,8 +39,10 @@ __device__ __forceinline__ float2 kahan_add(float2 a, float p)
 
 // ------------------------------------------------------------------ schedule (host)
 
-bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *srs, std::vector<Stage> *sts)
+bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *srs, std::vector<Stage> *sts,
+                          int span)
 {
+    if (span < kMinSpan || span > kMaxSpan) return false;
     srs->clear();
     sts->clear();
     int j = 0;
@@ -55,9 +57,12 @@ bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<Sub
         j = j0 + len;
     }
     // SPAN: the widest delay range of one stage (measured on GB300 with K = 512 and 1024 slot
-    // rows: 240 runs the 200 log delays 1..2000 2 % faster than 112 and sparse delays 64 apart 9 %
-    // faster; 320 and more slow both, their copy groups leaving too few free rows to prefetch)
-    const int K = kDelayBlock, SB = kSlotBuf, SPAN = 240;
+    // rows and one writer warp: 240 ran the 200 log delays 1..2000 2 % faster than 112 and sparse
+    // delays 64 apart 9 % faster; 320 and more slowed both, their copy groups leaving too few free
+    // rows to prefetch).  The default; a context may measure the best span for its own delay list
+    // (NFS_OPT_DELAY_SPAN = 0).  The span groups sub-runs into copy stages only: the pair
+    // arithmetic and the batches of partial sums, so the results, do not depend on it.
+    const int K = kDelayBlock, SB = kSlotBuf, SPAN = span;
     // needed frame range of every consumer step, relative to t0: step 0 reads the block itself
     std::vector<int> need_lo(1, 0), need_hi(1, K - 1);
     // frames t0 + lo_prev .. are in the buffer after the block is loaded (a cross pass's block is

@@ -266,7 +266,7 @@ cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long l
     if (nf <= 0) return cudaSuccess;
     if constexpr (sizeof(T) == 4) {
         if (tws_row) {
-            cudaError_t e = launch_row_fft_ct(frames, nf, sums, ref, g, tws_row, tw_post, scratch, s);
+            cudaError_t e = launch_row_fft_ct(frames, nf, sums, ref, g, tws_row, tw_post, scratch, s, tw_row);
             if (e != cudaErrorNotSupported) return e;
             cudaGetLastError();
         }

@@ -325,6 +325,130 @@ __global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__
     }
 }
 
+// Row pass of 2048-wide frames, one warp per row.  The packed row z[n] = p[2n] + i p[2n+1]
+// (1024 points) is transformed as 32 x 32 (n = 32 n1 + n2, k = k1 + 32 k2):
+//   lane n2 takes the 32-point DFT over n1 in registers and multiplies by W_1024^(n2 k1);
+//   the 32 x 32 values pass once through shared memory (padded rows: both the store and the load
+//   are two wavefronts per warp);
+//   lane k1 takes the 32-point DFT over n2, giving Z[k1 + 32 k2] in its register k2.
+// The real-to-complex split X[k] = E + W_2048^k O (E, O from Z[k] and conj Z[1024 - k]) finds
+// Z[1024 - k] in lane (32 - k1) mod 32, register 31 - k2 (lane 0: its own register (32 - k2) mod
+// 32), read with a warp shuffle.  One shared-memory round trip per row instead of one per radix
+// stage.
+constexpr int kRowWarpsW = 4;  // rows (warps) per CTA
+
+// W_32^j = exp(-2 pi i j / 32), j < 22 (the twiddles of the 8 x 4 decomposition below)
+__constant__ float2 kW32[22] = {
+    {1.0f, 0.0f}, {0.98078528040323043f, -0.19509032201612825f}, {0.92387953251128674f, -0.38268343236508978f},
+    {0.83146961230254524f, -0.55557023301960218f}, {0.70710678118654757f, -0.70710678118654746f}, {0.55557023301960229f, -0.83146961230254524f},
+    {0.38268343236508984f, -0.92387953251128674f}, {0.19509032201612833f, -0.98078528040323043f}, {0.0f, -1.0f},
+    {-0.19509032201612819f, -0.98078528040323043f}, {-0.38268343236508973f, -0.92387953251128674f}, {-0.55557023301960196f, -0.83146961230254546f},
+    {-0.70710678118654746f, -0.70710678118654757f}, {-0.83146961230254535f, -0.55557023301960218f}, {-0.92387953251128674f, -0.38268343236508989f},
+    {-0.98078528040323043f, -0.19509032201612861f}, {-1.0f, 0.0f}, {-0.98078528040323043f, 0.19509032201612836f},
+    {-0.92387953251128685f, 0.38268343236508967f}, {-0.83146961230254546f, 0.55557023301960196f}, {-0.70710678118654768f, 0.70710678118654746f},
+    {-0.55557023301960218f, 0.83146961230254524f}};
+
+// In-register 32-point DFT, natural order in and out: 32 = 8 x 4 (n = 4 m + r, k = k' + 8 k''),
+// eight-point transforms over m, twiddles W_32^(r k'), four-point transforms over r.
+__device__ __forceinline__ void dft32(float2 (&v)[32])
+{
+    float2 y[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+#pragma unroll
+        for (int m = 0; m < 8; ++m) y[r][m] = v[4 * m + r];
+        Dft<8>::run(y[r]);
+#pragma unroll
+        for (int k = 1; k < 8; ++k)
+            if (r) y[r][k] = cmul(y[r][k], kW32[r * k]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        float2 u[4] = {y[0][k], y[1][k], y[2][k], y[3][k]};
+        Dft<4>::run(u);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[k + 8 * q] = u[q];
+    }
+}
+
+__global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint16_t *__restrict__ frames,
+                                                                       const unsigned long long *__restrict__ sums,
+                                                                       const float *__restrict__ ref, Geometry g,
+                                                                       const float2 *__restrict__ tw,
+                                                                       const float2 *__restrict__ twp,
+                                                                       float2 *__restrict__ scratch)
+{
+    __shared__ __align__(16) float2 tr[kRowWarpsW][32][33];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int f = blockIdx.y;
+    const int y = blockIdx.x * kRowWarpsW + wq;
+    if (y >= g.H) return;  // warp-private work: no CTA barrier follows
+    const unsigned long long S = sums[f];
+    const double invd = S ? (double)g.HW / (double)S : 0.0;
+    // 1/<i> as a float pair; the reference subtraction sits inside the first FMA (see k_fft.cu)
+    const float inv_hi = (float)invd;
+    const float inv_lo = (float)(invd - (double)inv_hi);
+    const unsigned *fr = reinterpret_cast<const unsigned *>(frames + (size_t)f * g.HW + (size_t)y * 2048);
+    const float2 *rf = reinterpret_cast<const float2 *>(ref + (size_t)y * 2048);
+    float2 v[32];
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) {
+        const unsigned raw = __ldg(fr + 32 * n1 + lane);
+        const float2 r = __ldg(rf + 32 * n1 + lane);
+        const float a = (float)(raw & 0xffffu), b = (float)(raw >> 16);
+        v[n1] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -r.x)), __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -r.y))};
+    }
+    dft32(v);
+    // W_1024^(n2 k1) with k1 = k' + 8 k'': W_1024^(n2 k') W_1024^(8 n2 k'')
+    float2 a8[8], b4[4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a8[k] = __ldg(tw + lane * k);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) b4[q] = __ldg(tw + ((8 * lane * q) & 1023));
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) {
+        const float2 w = (k1 >> 3) ? cmul(a8[k1 & 7], b4[k1 >> 3]) : a8[k1];
+        v[k1] = cmul(v[k1], w);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) tr[wq][k1][lane] = v[k1];
+    __syncwarp();
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = tr[wq][lane][n2];
+    dft32(v);  // v[k2] = Z[lane + 32 k2]
+
+    float2 *out = scratch + (size_t)f * g.H * g.Wp;
+    const float2 p1 = __ldg(twp + lane);  // W_2048^lane
+    const int src = (32 - lane) & 31;
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) {
+        float2 zc;
+        zc.x = __shfl_sync(0xffffffffu, v[31 - k2].x, src);
+        zc.y = __shfl_sync(0xffffffffu, v[31 - k2].y, src);
+        if (lane == 0) zc = v[(32 - k2) & 31];
+        zc.y = -zc.y;
+        const float2 zk = v[k2];
+        const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
+        const float2 d = csub(zk, zc);
+        const float2 O = {0.5f * d.y, -0.5f * d.x};
+        const float2 w = k2 ? cmul(p1, __ldg(twp + 32 * k2)) : p1;  // W_2048^(lane + 32 k2)
+        const int k = lane + 32 * k2;
+        out[((size_t)(k >> 1) * g.H + y) * 2 + (k & 1)] = cadd(E, cmul(w, O));
+    }
+    // k = 1024 (the Nyquist column, from Z[0]) and the zero padding columns 1025 .. Wp - 1
+    if (lane == 0) {
+        const float2 zk = v[0];
+        const float2 zc = {zk.x, -zk.y};
+        const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
+        const float2 d = csub(zk, zc);
+        const float2 O = {0.5f * d.y, -0.5f * d.x};
+        out[((size_t)512 * g.H + y) * 2] = cadd(E, cmul(__ldg(twp + 1024), O));
+    } else if (1024 + lane < g.Wp) {
+        const int k = 1024 + lane;
+        out[((size_t)(k >> 1) * g.H + y) * 2 + (k & 1)] = {0.f, 0.f};
+    }
+}
+
 // Threads of the column pass: the largest of 256, 128, 64 that divides the 2H points of a pair.
 __host__ __device__ constexpr int col_threads(int H)
 {
@@ -411,10 +535,16 @@ static bool ct_size(int n)
 }
 
 cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
-                              const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch, cudaStream_t s)
+                              const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch, cudaStream_t s,
+                              const float2 *tw)
 {
     if (!tws || (reinterpret_cast<uintptr_t>(frames) & 3) || g.Wp != ((g.Lr + 1) + 3) / 4 * 4 || !ct_size(g.Lr))
         return cudaErrorNotSupported;
+    if (g.Lr == 1024 && tw) {  // one warp per row (the plan below: 4 shared-memory stages)
+        dim3 grid((g.H + ct::kRowWarpsW - 1) / ct::kRowWarpsW, nf);
+        ct::k_row_fft_w1024<<<grid, ct::kRowWarpsW * 32, 0, s>>>(frames, sums, ref, g, tw, twp, scratch);
+        return cudaGetLastError();
+    }
     switch (g.Lr) {
         case 64: return row_ct<64>(frames, nf, sums, ref, g, tws, twp, scratch, s);
         case 128: return row_ct<128>(frames, nf, sums, ref, g, tws, twp, scratch, s);

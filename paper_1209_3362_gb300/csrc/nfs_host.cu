@@ -403,6 +403,91 @@ int autotune_fft_chunk(nfs_ctx *c)
     return NFS_OK;
 }
 
+// The tiled kernel's schedule rebuilt with another stage span (NFS_EUNSUPPORTED, keeping the old
+// one, if the span is out of range or the schedule would not fit the kernel parameters).
+int set_delay_span(nfs_ctx *c, int span)
+{
+    if (!c->f32() || !c->sched) return NFS_EUNSUPPORTED;
+    std::vector<SubRun> srs;
+    std::vector<Stage> sts;
+    if (!build_delay_schedule(c->delays.data(), c->nd, c->cross, &srs, &sts, span)) return NFS_EUNSUPPORTED;
+    if (srs.size() > (size_t)kMaxSubRuns || sts.size() > (size_t)kMaxSchedStages) return NFS_EUNSUPPORTED;
+    c->sched->nsr = (int)srs.size();
+    c->sched->nst = (int)sts.size();
+    c->sched->nbatch = count_delay_batches(srs);
+    std::copy(srs.begin(), srs.end(), c->sched->sr);
+    std::copy(sts.begin(), sts.end(), c->sched->st);
+    c->span = span;
+    return NFS_OK;
+}
+
+// Stage span chosen by measurement on this context's delay list: each candidate runs the tiled
+// kernel in steady state (block t0 = tau_max, all stages active) over 8 tiles per SM of a zeroed
+// ring, twice after one warm-up launch; the fastest is kept.  The accumulators are cleared
+// afterwards (only before the first frame: the measurement uses the ring and the accumulators).
+int autotune_delay_span(nfs_ctx *c)
+{
+    if (!c->f32() || !c->sched || c->cross) return NFS_EUNSUPPORTED;
+    int n_sm = 0;
+    CK(c, cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, c->device));
+    const size_t tiles = std::min<size_t>(c->g.M / kTile, (size_t)8 * (size_t)std::max(n_sm, 1));
+    CK(c, cudaMemsetAsync(c->d_ring, 0, (size_t)c->R * c->g.M * c->csize(), c->stream));
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    const int cands[5] = {112, 176, 240, 320, 400};
+    const int start = c->span;
+    int best = start;
+    float best_ms = 1e30f;
+    int rc = NFS_OK;
+    for (int cand : cands) {
+        if (set_delay_span(c, cand) != NFS_OK) continue;
+        DelayArgs a;
+        a.ring = (const float2 *)c->d_ring;
+        a.R = c->R;
+        a.M = tiles * kTile;
+        a.t0 = c->tau_max;
+        a.nb = c->K;
+        a.delays = c->d_delays;
+        a.nd = c->nd;
+        a.acc = (float2 *)c->d_acc;
+        a.sched = c->sched;
+        a.err = c->d_err;
+        a.tau_max = c->tau_max;
+        a.stall_group = -1;
+        float tot = 0.f;
+        for (int rep = 0; rep < 3 && rc == NFS_OK; ++rep) {
+            if (cudaEventRecord(e0, c->stream) != cudaSuccess || launch_delay_f32(a, 0, c->stream) != cudaSuccess ||
+                cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = set_cuda_error(c, cudaGetLastError(), "span autotune");
+                break;
+            }
+            c->launches++;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) tot += ms;
+        }
+        if (rc) break;
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = cand;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    int dev_err = 0;
+    CK(c, cudaMemcpy(&dev_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (dev_err) {
+        c->errmsg = "span autotune: a bounded wait of the delay kernel gave up";
+        if (c->err == NFS_OK) c->err = NFS_ETIMEOUT;
+        return c->err;
+    }
+    CK(c, cudaMemsetAsync(c->d_acc, 0, (size_t)c->nd * c->g.M * c->asize(), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return set_delay_span(c, best);
+}
+
 // Frames the next chunk may take so that a chunk never spans two delay blocks.
 int next_chunk(const nfs_ctx *c, long long remaining, int cap)
 {
@@ -830,6 +915,13 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             if (v < -1 || v > 1000000) return NFS_EINVAL;
             c->stall_group = (int)v;
             return NFS_OK;
+        case NFS_OPT_DELAY_SPAN:
+            if (v == 0) {
+                if (c->nframes > 0 || c->have_ref) return NFS_ESTATE;
+                return autotune_delay_span(c);
+            }
+            if (v < kMinSpan || v > kMaxSpan) return NFS_EINVAL;
+            return set_delay_span(c, (int)v);
         default: return NFS_EINVAL;
     }
 }
@@ -849,6 +941,7 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_TEST_STALL_GROUP: *v = c->stall_group; return NFS_OK;
         case NFS_OPT_SLAB_FIRST_MODE: *v = (int64_t)c->g.k0; return NFS_OK;
         case NFS_OPT_SLAB_MODES: *v = (int64_t)c->g.M; return NFS_OK;
+        case NFS_OPT_DELAY_SPAN: *v = c->span; return NFS_OK;
         default: return NFS_EINVAL;
     }
 }

@@ -58,6 +58,7 @@ struct nfs_ctx {
     int fft_chunk = 4;
     int stage_frames = 1;
     int delay_variant = 0;
+    int span = nfs::kDefaultSpan;  // widest delay range of one copy stage of the tiled schedule
     int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
     int stall_group = -1; // test hook of the bounded-wait path (NFS_OPT_TEST_STALL_GROUP)
     bool own_streams = true;   // false for members of a batch (the batch owns the streams)
@@ -167,6 +168,8 @@ int flush_block(nfs_ctx *c);
 int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums);
 int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old, const unsigned long long *sums);
 int autotune_fft_chunk(nfs_ctx *c);
+int set_delay_span(nfs_ctx *c, int span);
+int autotune_delay_span(nfs_ctx *c);
 int next_chunk(const nfs_ctx *c, long long remaining, int cap);
 int enter(nfs_ctx *c);
 int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block);

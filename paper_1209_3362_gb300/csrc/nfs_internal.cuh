@@ -90,9 +90,11 @@ cudaError_t launch_row_fft(const uint16_t *frames, int nf, const unsigned long l
                            const float2 *tws_row = nullptr);
 
 // Compile-time-specialised FP32 passes; cudaErrorNotSupported for sizes without one.
+// tw: the W_L table of the generic kernels (the 2048-wide row pass, one warp per row, uses it;
+// NULL: the shared-memory Stockham kernels for every size).
 cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned long long *sums, const float *ref,
                               const Geometry &g, const float2 *tws, const float2 *twp, float2 *scratch,
-                              cudaStream_t s);
+                              cudaStream_t s, const float2 *tw = nullptr);
 cudaError_t launch_col_fft_ct(int nf, const Geometry &g, const float2 *tws, const float2 *scratch, float2 *ring,
                               int R, int slot0, cudaStream_t s);
 // Per-stage twiddle table of the specialised kernels for length L (stage s with sub-length NS and
@@ -138,8 +140,11 @@ constexpr int kDelayBlock = 512;   // K of the tiled kernel: 16 warps x 2 half-w
 constexpr int kSlotBuf = 1024;     // shared-memory slot ring of the tiled kernel (128-byte slots)
 // cross: a cross pass (the block's frames belong to one sequence, the older frames of every pair
 // to another, indexed alike; delay 0 is a real pair), see DelayArgs::ring_cur
+constexpr int kDefaultSpan = 240;           // widest delay range of one copy stage (default)
+constexpr int kMinSpan = 16;
+constexpr int kMaxSpan = kSlotBuf - kDelayBlock;  // a stage's group must fit the slot ring with the block
 bool build_delay_schedule(const int *delays, int nd, bool cross, std::vector<SubRun> *subruns,
-                          std::vector<Stage> *stages);
+                          std::vector<Stage> *stages, int span = kDefaultSpan);
 int count_delay_batches(const std::vector<SubRun> &subruns);  // batches the consumers hand to the writer
 
 // The schedule travels by value in the kernel parameters (constant bank): uniform, cached reads.

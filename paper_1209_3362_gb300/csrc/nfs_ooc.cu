@@ -209,14 +209,16 @@ int nfs_structure_function_out_of_core(int H, int W, const int32_t *delays, int 
 
 extern "C" int nfs_delay_schedule(const int32_t *delays, int n_delays, int cross, int32_t *subruns, int32_t *stages,
                                   int max_entries, int *n_subruns, int *n_stages, int *block_frames,
-                                  int *slot_rows, int *copy_barriers)
+                                  int *slot_rows, int *copy_barriers, int span)
 {
     if (!delays || n_delays <= 0 || !n_subruns || !n_stages) return NFS_EINVAL;
+    if (span != 0 && (span < kMinSpan || span > kMaxSpan)) return NFS_EINVAL;
     for (int j = 0; j < n_delays; ++j)
         if (delays[j] < 0 || delays[j] > kMaxDelay || (j && delays[j] <= delays[j - 1])) return NFS_EINVAL;
     std::vector<SubRun> srs;
     std::vector<Stage> sts;
-    if (!build_delay_schedule(delays, n_delays, cross != 0, &srs, &sts)) return NFS_EUNSUPPORTED;
+    if (!build_delay_schedule(delays, n_delays, cross != 0, &srs, &sts, span ? span : kDefaultSpan))
+        return NFS_EUNSUPPORTED;
     *n_subruns = (int)srs.size();
     *n_stages = (int)sts.size();
     if (block_frames) *block_frames = kDelayBlock;

@@ -98,3 +98,43 @@ def test_context_fit_recovers_the_relaxation_rate():
     sel = (q * q * w.Dc > 0.04) & (q * q * w.Dc < 0.8)
     rel = np.abs(G[sel] / (w.Dc * q[sel] ** 2) - 1.0)
     assert sel.sum() > 10 and np.median(rel) < 0.2, (sel.sum(), np.median(rel))
+
+
+@pytest.mark.gpu
+def test_fit_of_the_pipelines_own_structure_function():
+    """Eq. 1's fit on the library's own D(q, tau) (the pipeline half of the fit workload): 1000 frames
+    of 1024x1024 from the 1024x1024 workload's generator (Gamma = D q^2, D = 2 px^2/frame), 1024 q bins,
+    200 log delays 1..500 (consecutive up to 164).  Gamma starts at +-50 % of the generator's D q^2,
+    A and B from the data; Gauss-Newton (nfs_fit) and Adam through the autograd Function must recover
+    Gamma(q) over the bins these delays resolve, 0.1 <= q < 0.5 rad/px (Gamma tau from 0.02-0.5 at
+    tau = 1 to a plateau well before tau = 500).  Statistical: tolerances from the sequence's noise."""
+    import torch
+    import nfs_synth as S
+    import paper_1209_3362_gb300 as P
+    from paper_1209_3362_gb300 import fit as F
+    P.build()
+    w = S.WORKLOADS["ddm1024"]
+    delays = S.log_delays(1, 500, 200)
+    nq = 1024
+    src = S.workload_source(w, device="cuda")
+    with P.NFS(w.H, w.W, delays, nq) as ctx:
+        for o in range(0, w.N, 100):
+            ctx.push_frames_device(src.next_frames(min(100, w.N - o)))
+        r = ctx.structure_function()
+        q, D = r["q_mean"], r["D"]
+        truth = w.Dc * q * q
+        rng = np.random.default_rng(5)
+        G0 = truth * (1.0 + rng.uniform(-0.5, 0.5, nq)) + 1e-9
+        A0 = np.maximum((D[-1] - D[0]) / 2.0, 1e-9) * (1.0 + rng.uniform(-0.5, 0.5, nq))
+        B0 = np.maximum(D[0] / 4.0, 1e-9)
+        A, B, G = ctx.fit(A0, B0, G0, iters=200)
+    sel = (q >= 0.1) & (q < 0.5)
+    rel = np.abs(G[sel] / truth[sel] - 1.0)
+    assert sel.sum() > 100 and np.median(rel) < 0.05 and np.quantile(rel, 0.9) < 0.12, (np.median(rel), np.quantile(rel, 0.9))
+    dev = lambda x: torch.tensor(np.asarray(x, np.float32), device="cuda").contiguous()  # noqa: E731
+    Dt, tau = dev(D), dev(delays)
+    l0 = F.loss_and_grad(dev(A0), dev(B0), dev(G0), Dt, tau)[0]
+    A2, B2, G2, l2 = F.fit_adam(Dt, tau, dev(A0), dev(B0), dev(G0), steps=600)
+    assert float(torch.median(l2 / l0)) < 1e-3
+    rel2 = np.abs(G2.cpu().numpy()[sel] / truth[sel] - 1.0)
+    assert np.median(rel2) < 0.12 and np.quantile(rel2, 0.9) < 0.3, (np.median(rel2), np.quantile(rel2, 0.9))

@@ -43,10 +43,12 @@ def test_fuzz_host_entry_points(lib):
         sr = np.zeros((64, 3), np.int32)
         st = np.zeros((64, 5), np.int32)
         outs = [ctypes.c_int(0) for _ in range(5)]
+        span = int(rng.choice([0, 0, 15, 16, 100, 240, 512, 513, -1]))
         rc = lib.nfs_delay_schedule(dp, int(d.size), int(rng.integers(0, 2)), sr.ctypes.data, st.ctypes.data, 64,
-                                    *[ctypes.byref(o) for o in outs])
+                                    *[ctypes.byref(o) for o in outs], span)
         assert rc in CODES
-        valid = d.size > 0 and d[0] >= 0 and d[-1] <= 65536 and bool(np.all(np.diff(d) > 0))
+        valid = (d.size > 0 and d[0] >= 0 and d[-1] <= 65536 and bool(np.all(np.diff(d) > 0))
+                 and (span == 0 or 16 <= span <= 512))
         if not valid:
             assert rc == P.NFS_EINVAL
         # band planner (host only)

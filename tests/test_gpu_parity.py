@@ -166,8 +166,10 @@ def test_identical_frames_give_exact_zero():
     assert list(got["pair_counts"]) == [39, 38, 23, 1, 0]
 
 
-@pytest.mark.parametrize("H,W", [(384, 512), (96, 768), (768, 1024)])
+@pytest.mark.parametrize("H,W", [(384, 512), (96, 768), (768, 1024), (54, 2048), (6, 2048)])
 def test_radix3_shapes(oracle_lib, H, W):
+    """Radix-3 transform lengths, and 2048-wide frames whose heights are not a multiple of the row
+    kernel's 4 rows per block (the one-warp-per-row 2048-wide row pass)."""
     fr = S.OUFrameSource(H, W, 2.0, seed=H + W).frames_numpy(10)
     delays = [1, 2, 5, 9]
     nq = min(H, W) // 2
@@ -395,3 +397,52 @@ def test_all_delays_mode(oracle_lib):
     check_counts(got, ref)
     assert got["pair_counts"][-1] == 1
     assert rel_err(got, ref) <= TOL_F32
+
+
+def test_device_pushes_of_temporary_tensors():
+    """Frames generated on the GPU and pushed as temporaries: generation may still be running on
+    PyTorch's stream when the push is queued, and each tensor is dropped right after the call while
+    the library still reads it on its own stream (its memory at once wanted by the next batch's
+    generation).  The binding orders the library's stream after PyTorch's and keeps each tensor's
+    memory until the library's stream has read it, so the result equals one push of a persistent
+    tensor bit for bit."""
+    H, W, N = 128, 192, 300
+    delays, nq = [1, 2, 3, 10, 40, 200], 48
+    src = S.OUFrameSource(H, W, 1.3, seed=91, device="cuda")
+    frames = src.next_frames(N).clone()
+    with P.NFS(H, W, delays, nq) as ctx:
+        ctx.push_frames_device(frames)
+        ref = ctx.structure_function()
+    src = S.OUFrameSource(H, W, 1.3, seed=91, device="cuda")
+    with P.NFS(H, W, delays, nq) as ctx:
+        for o in range(0, N, 25):
+            ctx.push_frames_device(src.next_frames(25))  # still being written, and freed when the call returns
+        got = ctx.structure_function()
+    np.testing.assert_array_equal(got["D"], ref["D"])
+
+
+def test_delay_span_autotune_and_explicit_spans_are_bit_identical():
+    """The stage span regroups the delay kernel's copy stages only: the autotuned span and explicit
+    spans give the default's result bit for bit; the autotuner runs only before the first frame."""
+    H, W, N = 96, 128, 1300
+    delays, nq = S.log_delays(1, 1100, 60), 32
+    dev = S.OUFrameSource(H, W, 0.9, seed=93, device="cuda").next_frames(N)
+    results = {}
+    for span in (None, 0, 64, 176, 512):
+        with P.NFS(H, W, delays, nq) as ctx:
+            if span is not None:
+                ctx.set_option(P.OPT_DELAY_SPAN, span)
+                got_span = ctx.get_option(P.OPT_DELAY_SPAN)
+                assert got_span == span if span else got_span in (112, 176, 240, 320, 400)
+            else:
+                assert ctx.get_option(P.OPT_DELAY_SPAN) == 240
+            ctx.push_frames_device(dev)
+            results[span] = ctx.structure_function()
+            if span == 0:
+                with pytest.raises(P.NFSError) as e:
+                    ctx.set_option(P.OPT_DELAY_SPAN, 0)
+                assert e.value.status == P.NFS_ESTATE
+            with pytest.raises(P.NFSError):
+                ctx.set_option(P.OPT_DELAY_SPAN, 15)
+    for span, r in results.items():
+        np.testing.assert_array_equal(r["D"], results[None]["D"], err_msg=str(span))

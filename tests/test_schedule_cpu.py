@@ -131,3 +131,36 @@ def test_check_catches_an_early_group():
     bad["stages"][g][4] -= 1
     with pytest.raises(AssertionError):
         _simulate(d, False, bad)
+
+
+@pytest.mark.parametrize("span", [16, 64, 112, 176, 320, 400, 512])
+@pytest.mark.parametrize("cross", [False, True])
+def test_every_stage_span_is_safe(span, cross):
+    """The stage span the autotuner may choose regroups sub-runs into copy stages; every span keeps
+    the replay's invariants on named and seeded lists, and the sub-runs (hence the pair arithmetic
+    and the partial-sum batches) do not depend on it."""
+    lists = [S.log_delays(1, 2000, 200), list(range(1, 129)), list(range(64, 2049, 64)), S.log_delays(1, 500, 100)]
+    lists += _random_lists(20, 4242 + span + int(cross))
+    checked = 0
+    for d in lists:
+        try:
+            sc = P.delay_schedule(d, cross, span=span)
+            ref = P.delay_schedule(d, cross)
+        except P.NFSError:
+            continue
+        assert np.array_equal(sc["subruns"], ref["subruns"])
+        for s in sc["stages"]:  # no stage spans more than `span` delays
+            first, n = int(s[0]), int(s[1])
+            lo = int(sc["subruns"][first][2])
+            hi = int(sc["subruns"][first + n - 1][2] + sc["subruns"][first + n - 1][1] - 1)
+            assert hi - lo <= max(span, int(sc["subruns"][first][1]) - 1)
+        assert _simulate(d, cross, sc) >= 1
+        checked += 1
+    assert checked >= 15
+
+
+def test_span_limits():
+    with pytest.raises(P.NFSError):
+        P.delay_schedule([1, 2, 3], span=15)
+    with pytest.raises(P.NFSError):
+        P.delay_schedule([1, 2, 3], span=513)
