@@ -62,8 +62,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "9344ab38761a7985f5030c9d2dad1fd99faf99fa3e770138c0fb93ce5474440e",
-                         "dram_bytes_per_alg_byte": 0.9969}
+NCU_DELAY_CALIBRATION = {"sha256": "ddca6ce58c1435465480048655d091b9b0a4a358fe85a7bcef3b243149d94ff1",
+                         "dram_bytes_per_alg_byte": 0.9964}
 
 
 def delay_kernel_sha():
@@ -259,6 +259,7 @@ def main():
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--delay-variant", type=int, default=0, help="fused delay kernel variant (0 = default)")
     ap.add_argument("--span", type=int, default=0, help="delay-kernel stage span (0 = choose by measurement)")
+    ap.add_argument("--fft-chunk", type=int, default=0, help="frames per FFT launch (0 = choose by measurement)")
     ap.add_argument("--replicas", action="store_true", help="N > 1: independent sequences per rank (weak scaling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
@@ -347,6 +348,7 @@ def main():
         ctx.set_option(P.OPT_DELAY_VARIANT, args.delay_variant)
     if not args.delay_variant:
         ctx.set_option(P.OPT_DELAY_SPAN, args.span)  # 0: measured on this delay list (results do not change)
+    ctx.set_option(P.OPT_FFT_CHUNK, args.fft_chunk)  # 0: frames per FFT launch measured for this shape
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
     ctx_span = ctx.get_option(P.OPT_DELAY_SPAN)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
@@ -453,8 +455,23 @@ def main():
         for _ in range(args.steps):
             step_host()
         e2e_s = ranks_max((time.perf_counter() - t0) / args.steps)
+        # one more (untimed) pass with the timeline trace: how the copies ran against the kernels
+        ctx.set_option(P.OPT_TIMING, 3)
+        ctx.reset_timings()
+        step_host()
+        tl = ctx.timeline()
+        ctx.set_option(P.OPT_TIMING, 0)
+        cp = [(a, b) for s_, a, b in tl if s_ == "h2d"]
+        chunk_bytes = w.N * w.H * w.W * 2 / max(len(cp), 1)
+        slow = [b - a for a, b in cp if chunk_bytes / ((b - a) / 1e3) / 1e9 < 100.0]
+        e2e_trace = {"copies": len(cp), "copies_below_100gbs": len(slow),
+                     "slow_copy_gb": round(len(slow) * chunk_bytes / 1e9, 2),
+                     "median_copy_gbs": float(np.median([chunk_bytes / ((b - a) / 1e3) / 1e9 for a, b in cp])) if cp else None,
+                     "first_delay_launch_ms": next((a for s_, a, b in tl if s_ == "delay"), None),
+                     "last_copy_end_ms": max((b for a, b in cp), default=None),
+                     "pass_end_ms": max((b for s_, a, b in tl), default=None)}
         e2e = {"value": job_value(1 if slabs else world, w.N, 1000.0 * e2e_s), "unit": "frames/s",
-               "h2d_bytes_per_step": int(w.N * w.H * w.W * 2),
+               "h2d_bytes_per_step": int(w.N * w.H * w.W * 2), "trace": e2e_trace,
                "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
         # the copy engines' rate from this process's page-locked buffer (1 GiB, alone on the GPU):
         # the end-to-end rate depends on it, and it varies with the box's state
@@ -514,7 +531,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
-                           "delay_span": ctx_span,
+                           "delay_span": ctx_span, "fft_chunk": ctx.get_option(P.OPT_FFT_CHUNK),
                            "parallelism": (f"mode-slabs{world}" if slabs else f"replicas{world}"),
                            "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "
