@@ -351,6 +351,7 @@ def main():
     ctx.set_option(P.OPT_FFT_CHUNK, args.fft_chunk)  # 0: frames per FFT launch measured for this shape
     K = ctx.get_option(P.OPT_BLOCK_FRAMES)
     ctx_span = ctx.get_option(P.OPT_DELAY_SPAN)
+    ctx_chunk = ctx.get_option(P.OPT_FFT_CHUNK)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
     stream = torch.cuda.ExternalStream(ctx.stream)
 
@@ -531,7 +532,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
-                           "delay_span": ctx_span, "fft_chunk": ctx.get_option(P.OPT_FFT_CHUNK),
+                           "delay_span": ctx_span, "fft_chunk": ctx_chunk,
                            "parallelism": (f"mode-slabs{world}" if slabs else f"replicas{world}"),
                            "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "

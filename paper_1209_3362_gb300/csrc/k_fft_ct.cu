@@ -371,6 +371,23 @@ __device__ __forceinline__ void dft32(float2 (&v)[32])
     }
 }
 
+// Output columns of a 2048-wide row (W/2 + 1 rounded up to 4) and the CTA-wide store of its rows to
+// the column-pair scratch: element (kp, r, c) goes to ((kp H + y0 + r) 2 + c), so the CTA's four
+// consecutive rows of one column pair are one 64-byte run (a row stored alone gives 16-byte runs).
+constexpr int kRowPitchW = 1028;
+static_assert(kRowWarpsW == 4, "store_rows indexes 4 rows x 2 columns per column pair");
+static_assert(kRowWarpsW * kRowPitchW <= kRowWarpsW * 32 * 33, "output rows fit the transpose buffer");
+__device__ __forceinline__ void store_rows(float2 (&tr)[kRowWarpsW][32][33], const Geometry &g, int y0,
+                                           float2 *__restrict__ out)
+{
+    const float2 *rows = &tr[0][0][0];
+    for (int e = threadIdx.x; e < kRowWarpsW * kRowPitchW; e += kRowWarpsW * 32) {
+        const int c = e & 1, r = (e >> 1) & (kRowWarpsW - 1), kp = e >> 3;
+        const int y = y0 + r;
+        if (y < g.H) out[((size_t)kp * g.H + y) * 2 + c] = rows[r * kRowPitchW + 2 * kp + c];
+    }
+}
+
 __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint16_t *__restrict__ frames,
                                                                        const unsigned long long *__restrict__ sums,
                                                                        const float *__restrict__ ref, Geometry g,
@@ -381,8 +398,14 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
     __shared__ __align__(16) float2 tr[kRowWarpsW][32][33];
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
     const int f = blockIdx.y;
-    const int y = blockIdx.x * kRowWarpsW + wq;
-    if (y >= g.H) return;  // warp-private work: no CTA barrier follows
+    const int y0 = blockIdx.x * kRowWarpsW;
+    const int y = y0 + wq;
+    if (y >= g.H) {  // rows past the frame: only the CTA's two barriers below
+        __syncthreads();
+        __syncthreads();
+        store_rows(tr, g, y0, scratch + (size_t)f * g.H * g.Wp);
+        return;
+    }
     const unsigned long long S = sums[f];
     const double invd = S ? (double)g.HW / (double)S : 0.0;
     // 1/<i> as a float pair; the reference subtraction sits inside the first FMA (see k_fft.cu)
@@ -417,7 +440,9 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
     for (int n2 = 0; n2 < 32; ++n2) v[n2] = tr[wq][lane][n2];
     dft32(v);  // v[k2] = Z[lane + 32 k2]
 
-    float2 *out = scratch + (size_t)f * g.H * g.Wp;
+    // every warp is done with its transpose tile: the CTA's buffer now takes its four output rows
+    __syncthreads();
+    float2 *row = &tr[0][0][0] + wq * kRowPitchW;
     const float2 p1 = __ldg(twp + lane);  // W_2048^lane
     const int src = (32 - lane) & 31;
 #pragma unroll
@@ -432,8 +457,7 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
         const float2 d = csub(zk, zc);
         const float2 O = {0.5f * d.y, -0.5f * d.x};
         const float2 w = k2 ? cmul(p1, __ldg(twp + 32 * k2)) : p1;  // W_2048^(lane + 32 k2)
-        const int k = lane + 32 * k2;
-        out[((size_t)(k >> 1) * g.H + y) * 2 + (k & 1)] = cadd(E, cmul(w, O));
+        row[lane + 32 * k2] = cadd(E, cmul(w, O));
     }
     // k = 1024 (the Nyquist column, from Z[0]) and the zero padding columns 1025 .. Wp - 1
     if (lane == 0) {
@@ -442,11 +466,12 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
         const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
         const float2 d = csub(zk, zc);
         const float2 O = {0.5f * d.y, -0.5f * d.x};
-        out[((size_t)512 * g.H + y) * 2] = cadd(E, cmul(__ldg(twp + 1024), O));
-    } else if (1024 + lane < g.Wp) {
-        const int k = 1024 + lane;
-        out[((size_t)(k >> 1) * g.H + y) * 2 + (k & 1)] = {0.f, 0.f};
+        row[1024] = cadd(E, cmul(__ldg(twp + 1024), O));
+    } else if (1024 + lane < kRowPitchW) {
+        row[1024 + lane] = {0.f, 0.f};
     }
+    __syncthreads();
+    store_rows(tr, g, y0, scratch + (size_t)f * g.H * g.Wp);
 }
 
 // Threads of the column pass: the largest of 256, 128, 64 that divides the 2H points of a pair.
@@ -540,7 +565,7 @@ cudaError_t launch_row_fft_ct(const uint16_t *frames, int nf, const unsigned lon
 {
     if (!tws || (reinterpret_cast<uintptr_t>(frames) & 3) || g.Wp != ((g.Lr + 1) + 3) / 4 * 4 || !ct_size(g.Lr))
         return cudaErrorNotSupported;
-    if (g.Lr == 1024 && tw) {  // one warp per row (the plan below: 4 shared-memory stages)
+    if (g.Lr == 1024 && tw && g.Wp == ct::kRowPitchW) {  // one warp per row (the plan below: 4 shared-memory stages)
         dim3 grid((g.H + ct::kRowWarpsW - 1) / ct::kRowWarpsW, nf);
         ct::k_row_fft_w1024<<<grid, ct::kRowWarpsW * 32, 0, s>>>(frames, sums, ref, g, tw, twp, scratch);
         return cudaGetLastError();
