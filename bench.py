@@ -324,22 +324,6 @@ def main():
     del src
     torch.cuda.synchronize()
     t_gen = time.perf_counter() - t_gen
-    # the pinned host copy for the end-to-end run, allocated before the library's own allocations
-    # and written by the CPU (as an acquisition program holds its frame buffer and writes frames
-    # into it): the frames pass through a small page-locked staging buffer.  (On some boxes a large
-    # page-locked buffer written only by the GPU's copy engines was read back 10-20x slower for
-    # its first few GB; see the end-to-end notes of the design.)
-    host = None
-    if not args.no_e2e:
-        host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
-        stg = torch.empty((64, w.H, w.W), dtype=torch.int16, pin_memory=True)
-        for o in range(0, w.N, 64):
-            n = min(64, w.N - o)
-            stg[:n].copy_(frames[o:o + n])
-            torch.cuda.synchronize()
-            host[o:o + n].copy_(stg[:n])
-        del stg
-
     if slabs:
         ctx = P.NFS(w.H, w.W, w.delays, w.n_qbins, slab=rank, n_slabs=world)
     else:
@@ -353,6 +337,22 @@ def main():
     ctx_span = ctx.get_option(P.OPT_DELAY_SPAN)
     ctx_chunk = ctx.get_option(P.OPT_FFT_CHUNK)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
+    # the pinned host copy for the end-to-end run, written by the CPU (as an acquisition program
+    # writes frames into its buffer) through a small page-locked staging buffer.  It is allocated
+    # after the library's context: on this pool a 33.5 GB page-locked buffer allocated before it
+    # had its first ~4.6 GB read 6-25x slower by the copy engines, every pass (the slow chunks
+    # follow the buffer's offsets, not the pass's start), while one allocated later was read at
+    # the full 211 GB/s throughout.
+    host = None
+    if not args.no_e2e:
+        host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
+        stg = torch.empty((64, w.H, w.W), dtype=torch.int16, pin_memory=True)
+        for o in range(0, w.N, 64):
+            n = min(64, w.N - o)
+            stg[:n].copy_(frames[o:o + n])
+            torch.cuda.synchronize()
+            host[o:o + n].copy_(stg[:n])
+        del stg
     stream = torch.cuda.ExternalStream(ctx.stream)
 
     def finish():
