@@ -262,6 +262,8 @@ def main():
     ap.add_argument("--fft-chunk", type=int, default=0, help="frames per FFT launch (0 = choose by measurement)")
     ap.add_argument("--replicas", action="store_true", help="N > 1: independent sequences per rank (weak scaling)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--h2d", choices=("sm", "ce"), default="sm",
+                    help="end-to-end host pushes: read by the SMs (library default) or by the copy engines")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
@@ -338,11 +340,10 @@ def main():
     ctx_chunk = ctx.get_option(P.OPT_FFT_CHUNK)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
     # the pinned host copy for the end-to-end run, written by the CPU (as an acquisition program
-    # writes frames into its buffer) through a small page-locked staging buffer.  It is allocated
-    # after the library's context: on this pool a 33.5 GB page-locked buffer allocated before it
-    # had its first ~4.6 GB read 6-25x slower by the copy engines, every pass (the slow chunks
-    # follow the buffer's offsets, not the pass's start), while one allocated later was read at
-    # the full 211 GB/s throughout.
+    # writes frames into its buffer) through a small page-locked staging buffer.  The library's
+    # host push reads it with the SMs (NFS_OPT_H2D = 0): the copy engines read the first ~4.6 GB of
+    # such a 33.5 GB buffer 6-25x slower than the rest on every pass, wherever it was allocated,
+    # while loads from the SMs read the same pages at full speed.
     host = None
     if not args.no_e2e:
         host = torch.empty((w.N, w.H, w.W), dtype=torch.int16, pin_memory=True)
@@ -444,6 +445,7 @@ def main():
         torch.cuda.empty_cache()
         frames = None
         ctx.set_option(P.OPT_TIMING, 0)
+        ctx.set_option(P.OPT_H2D, 0 if args.h2d == "sm" else 1)
 
         def step_host():
             ctx.reset()
@@ -472,7 +474,7 @@ def main():
                      "last_copy_end_ms": max((b for a, b in cp), default=None),
                      "pass_end_ms": max((b for s_, a, b in tl), default=None)}
         e2e = {"value": job_value(1 if slabs else world, w.N, 1000.0 * e2e_s), "unit": "frames/s",
-               "h2d_bytes_per_step": int(w.N * w.H * w.W * 2), "trace": e2e_trace,
+               "h2d_bytes_per_step": int(w.N * w.H * w.W * 2), "h2d": args.h2d, "trace": e2e_trace,
                "d2h_bytes_per_step": int(len(w.delays) * w.n_qbins * 8)}
         # the copy engines' rate from this process's page-locked buffer (1 GiB, alone on the GPU):
         # the end-to-end rate depends on it, and it varies with the box's state

@@ -203,6 +203,15 @@ void *nfs_get_stream(const nfs_ctx *ctx);
                                    ring and clears the accumulators afterwards, NFS_ESTATE once frames
                                    were pushed).  The span regroups copy stages only: results are
                                    bit-identical for every span */
+#define NFS_OPT_H2D 13           /* how host pushes reach the device: 0 = the SMs read page-locked
+                                    sources directly (a copy kernel on the copy stream, counted as a
+                                    launch; default); 1 = the copy engines (cudaMemcpyAsync).  Sources
+                                    that are not page-locked, or whose address or size is not a
+                                    multiple of 16 bytes, always go through the copy engines.  Both
+                                    move the same bytes: results are identical.  The SMs read at full
+                                    speed whatever state the host pages are in; the copy engines were
+                                    measured at 8-38 GB/s on the first gigabytes of some freshly
+                                    pinned buffers */
 #define NFS_OPT_SLAB_FIRST_MODE 10 /* read-only: first mode (column-major order) of a slab context */
 #define NFS_OPT_SLAB_MODES 11      /* read-only: modes held (the slab's share, a multiple of 16) */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);

@@ -41,6 +41,7 @@ OPT_TEST_STALL_GROUP = 9
 OPT_SLAB_FIRST_MODE = 10
 OPT_SLAB_MODES = 11
 OPT_DELAY_SPAN = 12
+OPT_H2D = 13
 FIT_GAUSS_NEWTON = 0
 FIT_ADAM = 1
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")
@@ -591,7 +592,13 @@ class NFSRoi(NFSBatch):
         self._inflight = _InFlight()
 
     def push_frames(self, frames):
-        """frames: [n, H, W] full frames in host memory."""
+        """frames: [n, H, W] full frames in host memory (numpy, or a CPU torch tensor, pinned or not)."""
+        if hasattr(frames, "data_ptr"):
+            t = frames
+            assert not t.is_cuda and t.is_contiguous() and t.element_size() == 2
+            assert tuple(t.shape[1:]) == (self.H, self.W)
+            self._check(self._L.nfs_roi_push(self._h, ctypes.c_void_p(t.data_ptr()), t.shape[0]), "nfs_roi_push")
+            return
         a = np.ascontiguousarray(frames, dtype=np.uint16)
         assert a.shape[1:] == (self.H, self.W)
         self._check(self._L.nfs_roi_push(self._h, _ptr(a), a.shape[0]), "nfs_roi_push")

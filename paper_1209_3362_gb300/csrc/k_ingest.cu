@@ -1,12 +1,46 @@
-// Ingest kernels: the exact spatial sum of every frame (for the mean normalisation of the
-// differential analysis: images are divided by their spatial average) and the FP32 reference
-// image subtracted before the FP32 transform.
+// Ingest kernels: the copy of pushed frames from page-locked host memory, the exact spatial sum of
+// every frame (for the mean normalisation of the differential analysis: images are divided by their
+// spatial average) and the FP32 reference image subtracted before the FP32 transform.
 #include <algorithm>
 
 #include "nfs_internal.cuh"
 #include "roi.cuh"
 
 namespace nfs {
+
+// Host-to-device frame copy read by the SMs: page-locked host memory is addressed directly (unified
+// addressing) and copied 16 bytes per thread per step into device memory.  Used instead of the
+// copy engines for host pushes: on GB300 machines the copy engines read some page-locked buffers at
+// 8-38 GB/s for their first gigabytes while loads from the SMs read the same pages at full speed
+// (and a few dozen CTAs of this kernel reach the ~210 GB/s the copy engines reach at best).  It
+// uses no shared memory and CTAs of 128 threads (4096 registers), so one fits beside a CTA of the
+// delay kernel on every SM.
+__global__ void __launch_bounds__(kGatherThreads) k_gather_h2d(const uint4 *__restrict__ src, uint4 *__restrict__ dst, size_t n16)
+{
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // four independent 16-byte loads in flight per thread
+    for (; i + 3 * stride < n16; i += 4 * stride) {
+        const uint4 a = src[i], b = src[i + stride], c = src[i + 2 * stride], d = src[i + 3 * stride];
+        dst[i] = a;
+        dst[i + stride] = b;
+        dst[i + 2 * stride] = c;
+        dst[i + 3 * stride] = d;
+    }
+    for (; i < n16; i += stride) dst[i] = src[i];
+}
+
+cudaError_t launch_gather_h2d(const void *host_src, void *dst, size_t bytes, cudaStream_t s)
+{
+    if (bytes == 0) return cudaSuccess;
+    if (((reinterpret_cast<uintptr_t>(host_src) | reinterpret_cast<uintptr_t>(dst) | bytes) & 15) != 0)
+        return cudaErrorInvalidValue;  // the caller falls back to the copy engines
+    const size_t n16 = bytes / 16;
+    const size_t want = (n16 + 4 * kGatherThreads - 1) / (4 * kGatherThreads);
+    const unsigned grid = (unsigned)std::min<size_t>(kGatherCtas, std::max<size_t>(want, 1));
+    k_gather_h2d<<<grid, kGatherThreads, 0, s>>>(reinterpret_cast<const uint4 *>(host_src), reinterpret_cast<uint4 *>(dst), n16);
+    return cudaGetLastError();
+}
 
 // sums[blockIdx.y] += sum of the frame's pixels.  Integer arithmetic, so the result is exact and
 // independent of the order of the atomic adds.  VEC: 16-byte loads (frame start 16-byte aligned).

@@ -384,8 +384,8 @@ int nfs_roi_push(nfs_batch *b, const uint16_t *host, int n)
     for (long long done = 0; done < n;) {
         const int nc = (int)std::min<long long>(kRoiGroup, n - done);
         // stream-ordered after the previous group's crop, which reads d_full
-        cudaError_t e = cudaMemcpyAsync(b->d_full, host + (size_t)done * HW, sizeof(uint16_t) * HW * nc,
-                                        cudaMemcpyHostToDevice, b->stream);
+        cudaError_t e = copy_h2d(b->d_full, host + (size_t)done * HW, sizeof(uint16_t) * HW * nc, b->stream,
+                                 locked, &b->launches);
         if (e != cudaSuccess) return batch_fail(b, e, "region-of-interest upload");
         if ((rc = nfs_roi_push_device(b, b->d_full, nc))) return rc;
         done += nc;

@@ -640,6 +640,28 @@ bool is_page_locked(const void *p)
     return at.type == cudaMemoryTypeHost;
 }
 
+const void *host_device_view(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
+cudaError_t copy_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s, bool sm_reads, long long *launches)
+{
+    if (sm_reads && ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15) == 0) {
+        if (const void *dev = host_device_view(src)) {
+            const cudaError_t e = launch_gather_h2d(dev, dst, bytes, s);
+            if (e == cudaSuccess && launches) ++*launches;
+            return e;
+        }
+    }
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s);
+}
+
 }  // namespace host
 }  // namespace nfs
 
@@ -728,7 +750,7 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
             src = c->h_stage[hs];
         }
         rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
-            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
+            return copy_h2d(dst, src, bytes, c->copy_stream, c->h2d == 0, &c->launches);
         }, "h2d");
         if (rc) return rc;
         if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
@@ -915,6 +937,10 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             if (v < -1 || v > 1000000) return NFS_EINVAL;
             c->stall_group = (int)v;
             return NFS_OK;
+        case NFS_OPT_H2D:
+            if (v < 0 || v > 1) return NFS_EINVAL;
+            c->h2d = (int)v;
+            return NFS_OK;
         case NFS_OPT_DELAY_SPAN:
             if (v == 0) {
                 if (c->nframes > 0 || c->have_ref) return NFS_ESTATE;
@@ -942,6 +968,7 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_SLAB_FIRST_MODE: *v = (int64_t)c->g.k0; return NFS_OK;
         case NFS_OPT_SLAB_MODES: *v = (int64_t)c->g.M; return NFS_OK;
         case NFS_OPT_DELAY_SPAN: *v = c->span; return NFS_OK;
+        case NFS_OPT_H2D: *v = c->h2d; return NFS_OK;
         default: return NFS_EINVAL;
     }
 }

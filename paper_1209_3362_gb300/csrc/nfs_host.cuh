@@ -61,6 +61,7 @@ struct nfs_ctx {
     int span = nfs::kDefaultSpan;  // widest delay range of one copy stage of the tiled schedule
     int fft_generic = 0;  // 1: generic FFT kernels even where specialised ones exist
     int stall_group = -1; // test hook of the bounded-wait path (NFS_OPT_TEST_STALL_GROUP)
+    int h2d = 0;          // host pushes: 0 = the SMs read page-locked sources, 1 = copy engines
     bool own_streams = true;   // false for members of a batch (the batch owns the streams)
     bool defer_delay = false;  // members of a batch: the batch runs the delay update of full blocks
     int device = 0;
@@ -176,6 +177,12 @@ int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, i
 int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
                 bool cross = false, int slab = 0, int n_slabs = 1);
 bool is_page_locked(const void *p);
+// The device-side address of page-locked host memory p, nullptr if p is not page-locked.
+const void *host_device_view(const void *p);
+// One host-to-device copy of a frame push on stream s.  With sm_reads, a page-locked source and
+// 16-byte aligned addresses and size, the SMs read the host memory (launch_gather_h2d; ++*launches);
+// otherwise the copy engines copy it (cudaMemcpyAsync).
+cudaError_t copy_h2d(void *dst, const void *src, size_t bytes, cudaStream_t s, bool sm_reads, long long *launches);
 
 }  // namespace host
 }  // namespace nfs

@@ -69,6 +69,12 @@ bool make_slab(Geometry *g, int slab, int n_slabs);
 
 // --------------------------------------------------------------- launchers (stream-ordered)
 
+// Copy bytes from page-locked host memory to device memory with loads issued by the SMs (at most
+// kGatherCtas CTAs of kGatherThreads threads on stream s).  cudaErrorInvalidValue (nothing
+// launched) unless both addresses and the size are multiples of 16 bytes.
+constexpr int kGatherCtas = 128, kGatherThreads = 128;
+cudaError_t launch_gather_h2d(const void *host_src, void *dst, size_t bytes, cudaStream_t s);
+
 // sums[f] = sum of the pixels of frame f (exact, uint64) for f < nf.  sums must be zeroed.
 cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
                               cudaStream_t s);

@@ -102,7 +102,7 @@ int cross_push(nfs_ctx *c, const uint16_t *cur, const uint16_t *old, long long n
             src = c->h_stage[hs];
         }
         const int rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
-            return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, c->copy_stream);
+            return copy_h2d(dst, src, bytes, c->copy_stream, c->h2d == 0, &c->launches);
         }, "h2d");
         if (rc) return rc;
         if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
