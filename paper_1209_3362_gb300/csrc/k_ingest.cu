@@ -35,6 +35,12 @@ cudaError_t launch_gather_h2d(const void *host_src, void *dst, size_t bytes, cud
     if (bytes == 0) return cudaSuccess;
     if (((reinterpret_cast<uintptr_t>(host_src) | reinterpret_cast<uintptr_t>(dst) | bytes) & 15) != 0)
         return cudaErrorInvalidValue;  // the caller falls back to the copy engines
+    // the largest shared-memory carve-out, as the delay kernel's: an SM takes CTAs of a kernel
+    // that prefers another carve-out only once it has drained
+    // (set on every call: the attribute belongs to the current device)
+    const cudaError_t carve =
+        cudaFuncSetAttribute(k_gather_h2d, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (carve != cudaSuccess) return carve;
     const size_t n16 = bytes / 16;
     const size_t want = (n16 + 4 * kGatherThreads - 1) / (4 * kGatherThreads);
     const unsigned grid = (unsigned)std::min<size_t>(kGatherCtas, std::max<size_t>(want, 1));

@@ -141,7 +141,7 @@ int nfs_batch_create(int n_seq, const int *H, const int *W, const int32_t *delay
     b->n = n_seq;
     cudaDeviceGetAttribute(&b->n_sm, cudaDevAttrMultiProcessorCount, b->device);
     if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithPriority(&b->copy_stream, cudaStreamNonBlocking, copy_stream_priority()) != cudaSuccess) {
         batch_free(b);
         return NFS_ECUDA;
     }

@@ -561,7 +561,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     };
     if (!make_plan(c->g.Lr, &c->plan_row) || !make_plan(H, &c->plan_col)) return bail(NFS_EUNSUPPORTED);
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess)
+        cudaStreamCreateWithPriority(&c->copy_stream, cudaStreamNonBlocking, copy_stream_priority()) != cudaSuccess)
         return bail(NFS_ECUDA);
     // copy chunks of up to 256 MB; the device staging ring covers two delay blocks, at most 4 GB
     c->copy_frames = (int)std::max<size_t>(1, std::min<size_t>(64, (256u << 20) / c->frame_bytes()));
@@ -638,6 +638,18 @@ bool is_page_locked(const void *p)
         return false;
     }
     return at.type == cudaMemoryTypeHost;
+}
+
+int copy_stream_priority()
+{
+    // the greatest priority (numerically least): the copy kernel's CTAs are placed before the
+    // compute stream's pending CTAs as SMs free up
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return greatest;
 }
 
 const void *host_device_view(const void *p)

@@ -177,6 +177,8 @@ int check_args(int H, int W, const int32_t *delays, int n_delays, int n_qbins, i
 int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, int path, int block, nfs_ctx **out,
                 bool cross = false, int slab = 0, int n_slabs = 1);
 bool is_page_locked(const void *p);
+// Priority of the copy streams: the device's greatest.
+int copy_stream_priority();
 // The device-side address of page-locked host memory p, nullptr if p is not page-locked.
 const void *host_device_view(const void *p);
 // One host-to-device copy of a frame push on stream s.  With sm_reads, a page-locked source and
