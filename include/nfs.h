@@ -64,7 +64,8 @@ typedef struct nfs_ctx nfs_ctx;
  *   n_qbins   number of radial bins, 1..65536; bins span 0 <= |f| < 0.5 cycles/px evenly.
  *   *out      receives the context; NULL on failure.
  * Allocates the spectrum ring (tau_max + K slots of H x (W/2+1) complex values), the
- * accumulators (n_delays x H x (W/2+1)) and the staging buffers on the current device.
+ * accumulators (n_delays x H x (W/2+1)) and the staging buffers (copy chunks of up to 256 MB
+ * covering two delay blocks, at most 9 GB) on the current device.
  * Uses NFS_PATH_FUSED_F32.
  */
 int nfs_create(int H, int W, const int32_t *delays, int n_delays, int n_qbins, nfs_ctx **out);
@@ -117,8 +118,11 @@ int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_
  * Append n_frames frames from HOST memory, contiguous [n_frames][H][W] uint16, row-major.
  * Counts above 4095 are allowed (no clipping).  The frames are copied to the device before the
  * call returns, so the caller may reuse the buffer at once; the analysis itself runs
- * asynchronously on the context's stream.  Page-locked buffers are copied by DMA directly;
- * pageable ones pass through the context's pinned staging buffers.
+ * asynchronously on the context's stream.  Page-locked buffers are read directly (by the SMs or
+ * the copy engines: NFS_OPT_H2D); pageable ones pass through the context's pinned staging buffers.
+ * The copies run on a stream of the device's greatest priority, chunks of up to 256 MB into a
+ * device staging ring of two delay blocks; a slot transformed into the spectrum ring is handed
+ * back just before the next delay launch, so that its refill runs beside that launch.
  * A frame whose pixels sum to 0 has no mean: its normalised image is taken as 0.
  * A context takes at most 2^31 - 4096 frames between nfs_create/nfs_reset (frame indices in the
  * kernels are 32-bit): a push beyond that returns NFS_ESTATE and changes nothing.

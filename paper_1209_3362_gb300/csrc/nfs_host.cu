@@ -248,10 +248,19 @@ int alloc_dev(nfs_ctx *c, void **p, size_t bytes)
     return set_cuda_error(c, e, "cudaMalloc");
 }
 
+int release_slots(nfs_ctx *c)
+{
+    for (int s : c->free_pending) CK(c, cudaEventRecord(c->ev_free[s], c->stream));
+    c->free_pending.clear();
+    return NFS_OK;
+}
+
 int flush_block(nfs_ctx *c)
 {
     const long long nb = c->nframes - c->nprocessed;
     if (nb <= 0 || !c->f32()) return NFS_OK;
+    int rc = release_slots(c);  // recorded before the launch: the refills run beside it
+    if (rc) return rc;
     DelayArgs a;
     a.ring = (const float2 *)c->d_ring;
     a.R = c->R;
@@ -269,8 +278,8 @@ int flush_block(nfs_ctx *c)
         a.ring_cur = (const float2 *)c->d_ring_cur;
         a.R_cur = c->K;
     }
-    int rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
-                   "delay_f32");
+    rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
+               "delay_f32");
     if (rc) return rc;
     c->nprocessed = c->nframes;
     return NFS_OK;
@@ -563,10 +572,11 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithPriority(&c->copy_stream, cudaStreamNonBlocking, copy_stream_priority()) != cudaSuccess)
         return bail(NFS_ECUDA);
-    // copy chunks of up to 256 MB; the device staging ring covers two delay blocks, at most 4 GB
+    // copy chunks of up to 256 MB; the device staging ring covers two delay blocks, at most 9 GB
+    // (the copies of block b + 2 then run beside the delay launch of block b)
     c->copy_frames = (int)std::max<size_t>(1, std::min<size_t>(64, (256u << 20) / c->frame_bytes()));
     {
-        const size_t cap = std::max<size_t>(2, (size_t(4) << 30) / (c->frame_bytes() * (size_t)c->copy_frames));
+        const size_t cap = std::max<size_t>(2, (size_t(9) << 30) / (c->frame_bytes() * (size_t)c->copy_frames));
         const size_t want = std::max<size_t>(2, (2 * (size_t)c->K + c->copy_frames - 1) / c->copy_frames);
         c->n_slots = (int)std::min(cap, want);
     }
@@ -746,13 +756,18 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
     }
     long long done = 0;
     int last = -1;
+    // FP32 contexts that launch their own delay updates hold slot releases back to the next launch
+    const bool hold = c->f32() && !c->defer_delay;
     while (done < n) {
         const int nc = (int)std::min<long long>(c->copy_frames, n - done);
         const int slot = (int)(c->stage_i++ % c->n_slots);
         const size_t bytes = c->frame_bytes() * (size_t)nc;
         uint16_t *dst = c->d_stage + (size_t)slot * c->copy_frames * c->g.HW;
         const uint16_t *src = h + (size_t)done * c->g.HW;
-        // the kernels that read this slot last time must be done before it is overwritten
+        // the kernels that read this slot last time must be done before it is overwritten (a slot
+        // whose release is still held back is released now: the wait must see its latest use)
+        if (std::find(c->free_pending.begin(), c->free_pending.end(), slot) != c->free_pending.end())
+            if ((rc = release_slots(c))) return rc;
         CK(c, cudaStreamWaitEvent(c->copy_stream, c->ev_free[slot], 0));
         int hs = -1;
         if (!locked) {
@@ -775,10 +790,14 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
             if (rc) return rc;
             o += nf;
         }
-        CK(c, cudaEventRecord(c->ev_free[slot], c->stream));
+        if (hold)
+            c->free_pending.push_back(slot);
+        else
+            CK(c, cudaEventRecord(c->ev_free[slot], c->stream));
         done += nc;
         last = slot;
     }
+    if ((rc = release_slots(c))) return rc;
     // copies run in order on the copy stream: when the last one is done the caller's buffer is free
     if (locked && last >= 0) CK(c, cudaEventSynchronize(c->ev_filled[last]));
     return c->err;

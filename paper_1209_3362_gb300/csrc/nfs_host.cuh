@@ -74,6 +74,10 @@ struct nfs_ctx {
     // through two pinned host chunks first.
     int copy_frames = 1, n_slots = 2;
     uint16_t *d_stage = nullptr;
+    // Staging slots whose frames are transformed but whose release (ev_free) is held back until
+    // just before the next delay launch, so that the copies refilling them overlap that launch
+    // (where one copy CTA fits beside each delay CTA) instead of the transforms of the next block.
+    std::vector<int> free_pending;
     uint16_t *h_stage[2] = {nullptr, nullptr};
     std::vector<cudaEvent_t> ev_filled, ev_free;
     cudaEvent_t ev_hcopied[2] = {nullptr, nullptr};
@@ -166,6 +170,7 @@ int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
 }
 
 int flush_block(nfs_ctx *c);
+int release_slots(nfs_ctx *c);
 int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums);
 int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old, const unsigned long long *sums);
 int autotune_fft_chunk(nfs_ctx *c);
