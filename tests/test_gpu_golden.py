@@ -27,7 +27,7 @@ def fixture(name):
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("name", ["ddm1024"])
+@pytest.mark.parametrize("name", ["ddm1024", "ddm2048"])
 def test_full_size_sequence_matches_the_stored_oracle(name):
     import paper_1209_3362_gb300 as P
     P.build()
