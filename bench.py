@@ -256,6 +256,8 @@ def main():
     ap.add_argument("--H", type=int, default=0, help="override frame height (profiling cases; not a bench value)")
     ap.add_argument("--W", type=int, default=0, help="override frame width (profiling cases; not a bench value)")
     ap.add_argument("--delays", type=int, default=0, help="use delays 1..n (profiling cases; not a bench value)")
+    ap.add_argument("--delay-step", type=int, default=1,
+                    help="with --delays n: delays step, 2 step, .., n step (isolated delays; profiling cases)")
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--delay-variant", type=int, default=0, help="fused delay kernel variant (0 = default)")
     ap.add_argument("--span", type=int, default=0, help="delay-kernel stage span (0 = choose by measurement)")
@@ -277,7 +279,8 @@ def main():
     if args.frames or args.H or args.W or args.delays:
         import dataclasses
         w = dataclasses.replace(w, N=args.frames or w.N, H=args.H or w.H, W=args.W or w.W,
-                                delays=tuple(range(1, args.delays + 1)) if args.delays else w.delays)
+                                delays=tuple(range(args.delay_step, args.delays * args.delay_step + 1, args.delay_step))
+                                if args.delays else w.delays)
     if args.impl == "reference":
         return run_reference(args, w)
 

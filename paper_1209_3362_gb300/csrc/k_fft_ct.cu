@@ -254,6 +254,28 @@ __host__ __device__ constexpr int rows_per_cta(int L)
 
 // Row pass for frames of width W = 2L: RPC rows per CTA, 8 complex points per thread; output to
 // the column-pair scratch of frame blockIdx.y.
+// hw / S as an unevaluated float pair (hi + lo, about 46 bits), from FP32 arithmetic only: GB300's
+// FP64 pipe is narrow, and a double division in every thread of a row pass kept it 20 % busy.
+// Dekker's double-float reciprocal: S = s_hi + s_lo exactly (16-bit counts of at most 2^24
+// pixels give S < 2^40, so S - s_hi fits in 16 bits); q0 = hw / s_hi correctly rounded, whose remainder hw - q0 s_hi a fused multiply-add
+// gives exactly; one correction q1 = (hw - q0 S) / s_hi; (q0, q1) renormalised by a fast two-sum.
+__device__ __forceinline__ void inv_mean_pair(unsigned long long S, int hw, float &hi, float &lo)
+{
+    if (S == 0ull) {
+        hi = lo = 0.f;
+        return;
+    }
+    const float s_hi = __ull2float_rn(S);
+    const float s_lo = (float)((long long)S - (long long)s_hi);
+    const float h = (float)hw;
+    const float q0 = __fdiv_rn(h, s_hi);
+    float r = __fmaf_rn(-q0, s_hi, h);
+    r = __fmaf_rn(-q0, s_lo, r);
+    const float q1 = __fdiv_rn(r, s_hi);
+    hi = __fadd_rn(q0, q1);
+    lo = __fsub_rn(q1, __fsub_rn(hi, q0));
+}
+
 template <int L>
 __global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__ frames,
                                                     const unsigned long long *__restrict__ sums,
@@ -269,11 +291,9 @@ __global__ void __launch_bounds__(kNT) k_row_fft_ct(const uint16_t *__restrict__
     __shared__ __align__(16) float2 bufB[padded(N)];
     const int f = blockIdx.y;
     const int row0 = blockIdx.x * RPC;
-    const unsigned long long S = sums[f];
-    const double invd = S ? (double)g.HW / (double)S : 0.0;
     // 1/<i> as a float pair; the reference subtraction sits inside the first FMA (see k_fft.cu)
-    const float inv_hi = (float)invd;
-    const float inv_lo = (float)(invd - (double)inv_hi);
+    float inv_hi, inv_lo;
+    inv_mean_pair(sums[f], g.HW, inv_hi, inv_lo);
     const uint16_t *fr = frames + (size_t)f * g.HW;
     constexpr int W = 2 * L;
     unsigned raw[PER];
@@ -406,11 +426,9 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
         store_rows(tr, g, y0, scratch + (size_t)f * g.H * g.Wp);
         return;
     }
-    const unsigned long long S = sums[f];
-    const double invd = S ? (double)g.HW / (double)S : 0.0;
     // 1/<i> as a float pair; the reference subtraction sits inside the first FMA (see k_fft.cu)
-    const float inv_hi = (float)invd;
-    const float inv_lo = (float)(invd - (double)inv_hi);
+    float inv_hi, inv_lo;
+    inv_mean_pair(sums[f], g.HW, inv_hi, inv_lo);
     const unsigned *fr = reinterpret_cast<const unsigned *>(frames + (size_t)f * g.HW + (size_t)y * 2048);
     const float2 *rf = reinterpret_cast<const float2 *>(ref + (size_t)y * 2048);
     float2 v[32];
