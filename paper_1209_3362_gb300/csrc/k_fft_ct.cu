@@ -157,6 +157,16 @@ __host__ __device__ constexpr int tw_offset(int L, int NS)
     return off;
 }
 __host__ __device__ constexpr int padded(int x) { return x + (x >> 4); }
+// padded(x0 + r STEP) from xp0 = padded(x0): when STEP is a multiple of 16 the padding of the step
+// is exact (STEP / 16 more), so only one index per thread is padded at run time.
+template <int STEP>
+__device__ __forceinline__ int padded_step(int x0, int xp0, int r)
+{
+    if constexpr (STEP % 16 == 0)
+        return xp0 + r * (STEP + STEP / 16);
+    else
+        return padded(x0 + r * STEP);
+}
 
 // One Stockham stage on NB transforms of length L (element (b, i) at b*L + i, or i*NB + b when
 // BFAST; padded), NT threads.  INPLACE: in == out, all inputs are read before a barrier.
@@ -183,11 +193,11 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
         jj[p] = j;
         bb[p] = b;
         if (TOT % NT == 0 || g < TOT) {
+            // element i = j + r NBF sits at i NB + b (BFAST) or b L + i
+            constexpr int STEP = BFAST ? NBF * NB : NBF;
+            const int x0 = BFAST ? j * NB + b : b * L + j, xp0 = padded(x0);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = j + r * NBF;
-                v[p][r] = in[padded(BFAST ? i * NB + b : b * L + i)];
-            }
+            for (int r = 0; r < R; ++r) v[p][r] = in[padded_step<STEP>(x0, xp0, r)];
         }
     }
     if (INPLACE) __syncthreads();
@@ -215,12 +225,11 @@ __device__ __forceinline__ void stage(const float2 *in, float2 *out, const float
                 for (int r = 1; r < R; ++r) v[p][r] = cmul(v[p][r], tw[r]);
             }
             Dft<R>::run(v[p]);
-            const int base = (j / NS) * NS * R + k;
+            const int base = (j / NS) * NS * R + k;  // output i = base + r NS
+            constexpr int STEP = BFAST ? NS * NB : NS;
+            const int x0 = BFAST ? base * NB + b : b * L + base, xp0 = padded(x0);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const int i = base + r * NS;
-                out[padded(BFAST ? i * NB + b : b * L + i)] = v[p][r];
-            }
+            for (int r = 0; r < R; ++r) out[padded_step<STEP>(x0, xp0, r)] = v[p][r];
         }
     }
 }
@@ -514,16 +523,39 @@ __global__ void __launch_bounds__(col_threads(H)) k_col_fft_ct(Geometry g, const
     const int kp = blockIdx.x + g.kp0;
     const int slot = (slot0 + f) % R;
     const float2 *src = scratch + (size_t)f * H * g.Wp + (size_t)kp * H * 2;
+    const int t = threadIdx.x;
 #pragma unroll
-    for (int p = 0; p < PER; ++p) {
-        const int e = threadIdx.x + p * NT;
-        buf[padded(e)] = __ldg(src + e);  // e = y * 2 + c: the BFAST layout of two columns
-    }
+    for (int p = 0; p < PER; ++p)  // e = y * 2 + c: the BFAST layout of two columns
+        buf[padded_step<NT>(t, padded(t), p)] = __ldg(src + t + p * NT);
     __syncthreads();
     const float2 *Y = run_stages<H, 1, 2, true, true, NT>(buf, buf, tws);
+    if constexpr (H % NT == 0 && NT % kTile == 0 && H % kTile == 0) {
+        // element e = t + p NT is column c = p NT / H, row y = t + (p NT) mod H.  Its slab-local mode
+        // kl = kl0[c] + yoff (signed: negative below the slab) has tile floor(kl / 16) = floor(kl0 / 16)
+        // + yoff / 16 and lane kl mod 16 = t mod 16, because the column start and the slab's first
+        // mode (always) are multiples of the tile: the ring index is a per-column base plus R yoff.
+        if ((g.k0 & (kTile - 1)) == 0) {
+            long long kl0[2], base[2];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                kl0[c] = (long long)(2 * kp + c) * H + t - (long long)g.k0;
+                base[c] = ((kl0[c] >> kTileShift) * R + slot) * kTile + (t & (kTile - 1));
+            }
+            const int yp = padded(2 * t);
+#pragma unroll
+            for (int p = 0; p < PER; ++p) {
+                constexpr int CPER = H / NT;  // elements per column and thread
+                const int c = p / CPER, yoff = (p % CPER) * NT;
+                const long long kl = kl0[c] + yoff;
+                if (2 * kp + c < g.Wh && kl >= 0 && kl < (long long)g.M)
+                    ring[base[c] + (long long)R * yoff] = Y[padded_step<2 * NT>(2 * t, yp, p % CPER) + c];
+            }
+            return;
+        }
+    }
 #pragma unroll
     for (int p = 0; p < PER; ++p) {
-        const int e = threadIdx.x + p * NT;
+        const int e = t + p * NT;
         const int c = e / H, y = e % H;
         const int kx = 2 * kp + c;
         const size_t kl = (size_t)kx * H + y - g.k0;  // the slab's modes only
