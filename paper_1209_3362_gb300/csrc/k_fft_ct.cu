@@ -377,6 +377,19 @@ __constant__ float2 kW32[22] = {
     {-0.92387953251128685f, 0.38268343236508967f}, {-0.83146961230254546f, 0.55557023301960196f}, {-0.70710678118654768f, 0.70710678118654746f},
     {-0.55557023301960218f, 0.83146961230254524f}};
 
+// W_64^k = W_2048^(32 k), k < 32: the real-to-complex split's twiddle steps between a lane's
+// outputs, as float values of the same double cosines and sines as the post-processing table
+// (warp-uniform indices: constant-bank operands instead of 31 loads per lane and row)
+__constant__ float2 kW64[32] = {
+    {1.0f, -0.0f}, {0.9951847195625305f, -0.0980171412229538f}, {0.9807852506637573f, -0.19509032368659973f}, {0.9569403529167175f, -0.290284663438797f},
+    {0.9238795042037964f, -0.3826834261417389f}, {0.8819212913513184f, -0.4713967442512512f}, {0.8314695954322815f, -0.5555702447891235f}, {0.7730104327201843f, -0.6343932747840881f},
+    {0.7071067690849304f, -0.7071067690849304f}, {0.6343932747840881f, -0.7730104327201843f}, {0.5555702447891235f, -0.8314695954322815f}, {0.4713967442512512f, -0.8819212913513184f},
+    {0.3826834261417389f, -0.9238795042037964f}, {0.290284663438797f, -0.9569403529167175f}, {0.19509032368659973f, -0.9807852506637573f}, {0.0980171412229538f, -0.9951847195625305f},
+    {6.123234262925839e-17f, -1.0f}, {-0.0980171412229538f, -0.9951847195625305f}, {-0.19509032368659973f, -0.9807852506637573f}, {-0.290284663438797f, -0.9569403529167175f},
+    {-0.3826834261417389f, -0.9238795042037964f}, {-0.4713967442512512f, -0.8819212913513184f}, {-0.5555702447891235f, -0.8314695954322815f}, {-0.6343932747840881f, -0.7730104327201843f},
+    {-0.7071067690849304f, -0.7071067690849304f}, {-0.7730104327201843f, -0.6343932747840881f}, {-0.8314695954322815f, -0.5555702447891235f}, {-0.8819212913513184f, -0.4713967442512512f},
+    {-0.9238795042037964f, -0.3826834261417389f}, {-0.9569403529167175f, -0.290284663438797f}, {-0.9807852506637573f, -0.19509032368659973f}, {-0.9951847195625305f, -0.0980171412229538f}};
+
 // In-register 32-point DFT, natural order in and out: 32 = 8 x 4 (n = 4 m + r, k = k' + 8 k''),
 // eight-point transforms over m, twiddles W_32^(r k'), four-point transforms over r.
 __device__ __forceinline__ void dft32(float2 (&v)[32])
@@ -483,7 +496,7 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
         const float2 E = {0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y)};
         const float2 d = csub(zk, zc);
         const float2 O = {0.5f * d.y, -0.5f * d.x};
-        const float2 w = k2 ? cmul(p1, __ldg(twp + 32 * k2)) : p1;  // W_2048^(lane + 32 k2)
+        const float2 w = k2 ? cmul(p1, kW64[k2]) : p1;  // W_2048^(lane + 32 k2)
         row[lane + 32 * k2] = cadd(E, cmul(w, O));
     }
     // k = 1024 (the Nyquist column, from Z[0]) and the zero padding columns 1025 .. Wp - 1
