@@ -452,14 +452,19 @@ __global__ void __launch_bounds__(kRowWarpsW * 32, 4) k_row_fft_w1024(const uint
     float inv_hi, inv_lo;
     inv_mean_pair(sums[f], g.HW, inv_hi, inv_lo);
     const unsigned *fr = reinterpret_cast<const unsigned *>(frames + (size_t)f * g.HW + (size_t)y * 2048);
-    const float2 *rf = reinterpret_cast<const float2 *>(ref + (size_t)y * 2048);
+    // the reference image rebuilt from the reference frame's 2-byte counts: fl32(count) times its
+    // reciprocal mean's high part, the product k_reference stored (half the bytes of the floats)
+    const char *rb = reinterpret_cast<const char *>(ref);
+    const unsigned *rr = reinterpret_cast<const unsigned *>(rb + ref_raw_offset(g.HW)) + (size_t)y * 1024;
+    const float ref_hi = __ldg(reinterpret_cast<const float2 *>(rb + ref_inv_offset(g.HW))).x;
     float2 v[32];
 #pragma unroll
     for (int n1 = 0; n1 < 32; ++n1) {
         const unsigned raw = __ldg(fr + 32 * n1 + lane);
-        const float2 r = __ldg(rf + 32 * n1 + lane);
+        const unsigned rw = __ldg(rr + 32 * n1 + lane);
+        const float rx = __fmul_rn((float)(rw & 0xffffu), ref_hi), ry = __fmul_rn((float)(rw >> 16), ref_hi);
         const float a = (float)(raw & 0xffffu), b = (float)(raw >> 16);
-        v[n1] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -r.x)), __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -r.y))};
+        v[n1] = {__fmaf_rn(a, inv_lo, __fmaf_rn(a, inv_hi, -rx)), __fmaf_rn(b, inv_lo, __fmaf_rn(b, inv_hi, -ry))};
     }
     dft32(v);
     // W_1024^(n2 k1) with k1 = k' + 8 k'': W_1024^(n2 k') W_1024^(8 n2 k'')

@@ -100,29 +100,36 @@ cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g,
     return cudaGetLastError();
 }
 
-// ref[x] = fl32(i_f(x) / <i_f>) for the first frame f < nf whose sum is not 0 (a dark frame
-// normalises to the zero image, which would leave the static beam in every transform); the zero
-// image when all nf frames are dark.  Any fixed image would do (it cancels in every difference);
-// this one removes the static beam before the FP32 transform.
+// ref[x] = fl32(fl32(i_f(x)) * hi) for the first frame f < nf whose sum is not 0 (a dark frame
+// normalises to the zero image, which would leave the static beam in every transform), with
+// hi + lo = HW / sum(i_f) as a float pair; the zero image when all nf frames are dark.  Any fixed
+// image would do (it cancels in every difference); this one removes the static beam before the
+// FP32 transform.  raw (optional) receives i_f itself and inv (optional) {hi, lo}: a row pass that
+// reads the 2-byte counts and forms the same product gets the same image bit for bit.
 __global__ void k_reference(const uint16_t *__restrict__ frames, const unsigned long long *__restrict__ sums, int nf,
-                            size_t HW, float *__restrict__ ref)
+                            size_t HW, float *__restrict__ ref, uint16_t *__restrict__ raw, float2 *__restrict__ inv)
 {
     int f = 0;
     while (f < nf && sums[f] == 0) ++f;
     const unsigned long long S = f < nf ? sums[f] : 0;
-    const double inv = S ? (double)HW / (double)S : 0.0;
+    const double invd = S ? (double)HW / (double)S : 0.0;
+    const float hi = (float)invd, lo = (float)(invd - (double)hi);
     const uint16_t *frame = frames + (size_t)(f < nf ? f : 0) * HW;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += (size_t)gridDim.x * blockDim.x)
-        ref[i] = (float)((double)frame[i] * inv);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += (size_t)gridDim.x * blockDim.x) {
+        const uint16_t n = f < nf ? frame[i] : (uint16_t)0;
+        ref[i] = __fmul_rn((float)n, hi);
+        if (raw) raw[i] = n;
+    }
+    if (inv && blockIdx.x == 0 && threadIdx.x == 0) *inv = make_float2(hi, lo);
 }
 
 cudaError_t launch_reference(const uint16_t *frames, const unsigned long long *sums, int nf, const Geometry &g,
-                             float *ref, cudaStream_t s)
+                             float *ref, cudaStream_t s, uint16_t *raw, float2 *inv)
 {
     if (nf <= 0) return cudaErrorInvalidValue;
     int bx = (int)((g.HW + 255) / 256);
     if (bx > 1216) bx = 1216;
-    k_reference<<<bx, 256, 0, s>>>(frames, sums, nf, g.HW, ref);
+    k_reference<<<bx, 256, 0, s>>>(frames, sums, nf, g.HW, ref, raw, inv);
     return cudaGetLastError();
 }
 

@@ -295,8 +295,12 @@ int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums
                    "frame_sums");
     if (rc) return rc;
     if (!c->have_ref && c->f32()) {
-        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_reference(dsrc, sums, n, c->g, c->d_ref, c->stream); },
-                   "reference");
+        rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] {
+            char *base = reinterpret_cast<char *>(c->d_ref);
+            return launch_reference(dsrc, sums, n, c->g, c->d_ref, c->stream,
+                                    reinterpret_cast<uint16_t *>(base + ref_raw_offset(c->g.HW)),
+                                    reinterpret_cast<float2 *>(base + ref_inv_offset(c->g.HW)));
+        }, "reference");
         if (rc) return rc;
         c->have_ref = true;
     }
@@ -376,7 +380,7 @@ int autotune_fft_chunk(nfs_ctx *c)
     const int nfr = kMaxChunkF32;
     const int cands[6] = {1, 2, 4, 8, 16, 32};
     CK(c, cudaMemsetAsync(c->d_sums, 0, sizeof(unsigned long long) * kMaxChunk, c->stream));
-    CK(c, cudaMemsetAsync(c->d_ref, 0, sizeof(float) * c->g.HW, c->stream));
+    CK(c, cudaMemsetAsync(c->d_ref, 0, ref_buffer_bytes(c->g.HW), c->stream));
     CK(c, cudaMemsetAsync(c->d_stage, 0, c->frame_bytes() * nfr, c->stream));
     cudaEvent_t e0, e1;
     CK(c, cudaEventCreate(&e0));
@@ -594,7 +598,7 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
     const size_t acc_bytes = (size_t)c->nd * c->g.M * c->asize();
     // sums of up to two copy chunks (a cross pass stages one of each sequence)
     if ((rc = alloc_dev(c, (void **)&c->d_sums, sizeof(unsigned long long) * 2 * kMaxChunk))) return bail(rc);
-    if (c->f32() && (rc = alloc_dev(c, (void **)&c->d_ref, sizeof(float) * c->g.HW))) return bail(rc);
+    if (c->f32() && (rc = alloc_dev(c, (void **)&c->d_ref, ref_buffer_bytes(c->g.HW)))) return bail(rc);
     if ((rc = alloc_dev(c, &c->d_ring, ring_bytes))) return bail(rc);
     if (cross && (rc = alloc_dev(c, &c->d_ring_cur, (size_t)c->K * c->g.M * c->csize()))) return bail(rc);
     if ((rc = alloc_dev(c, &c->d_acc, acc_bytes))) return bail(rc);

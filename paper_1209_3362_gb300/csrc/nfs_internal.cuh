@@ -79,10 +79,16 @@ cudaError_t launch_gather_h2d(const void *host_src, void *dst, size_t bytes, cud
 cudaError_t launch_frame_sums(const uint16_t *frames, int nf, const Geometry &g, unsigned long long *sums,
                               cudaStream_t s);
 
-// ref[x] = fl32(i_f(x) / <i_f>): the FP32 normalised first frame f < nf whose sum is not 0 (zero
-// if all nf frames are dark).
+// ref[x] = fl32(fl32(i_f(x)) * hi), hi + lo = HW / sum(i_f) as a float pair: the FP32 normalised first
+// frame f < nf whose sum is not 0 (zero if all nf frames are dark).  A context's reference buffer
+// (ref_buffer_bytes) also keeps that frame's raw counts (raw, at ref_raw_offset) and {hi, lo} (inv, at
+// ref_inv_offset), so a row pass may rebuild the same image from 2-byte counts; raw and inv may be
+// NULL (the image alone).
 cudaError_t launch_reference(const uint16_t *frames, const unsigned long long *sums, int nf, const Geometry &g,
-                             float *ref, cudaStream_t s);
+                             float *ref, cudaStream_t s, uint16_t *raw = nullptr, float2 *inv = nullptr);
+__host__ __device__ inline size_t ref_raw_offset(size_t HW) { return 4 * HW; }
+__host__ __device__ inline size_t ref_inv_offset(size_t HW) { return (6 * HW + 15) / 16 * 16; }
+__host__ __device__ inline size_t ref_buffer_bytes(size_t HW) { return ref_inv_offset(HW) + 16; }
 
 // Row pass: for nf frames, normalise (and subtract ref when T = float) and transform every row.
 // FP32: writes the column-group scratch of frame f at scratch + f * H * Wp.  FP64: writes the
