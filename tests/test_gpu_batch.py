@@ -99,3 +99,35 @@ def test_batch_of_camera_shapes_matches_oracle(camera_shapes):
             ctx.push_frames_device(dev[s])
             single = ctx.structure_function()
         np.testing.assert_array_equal(got[s]["D"], single["D"])
+
+
+def test_ragged48_workload_matches_oracle_on_its_small_members(oracle_lib):
+    """The ragged benchmark workload itself (48 sequences x 500 frames of the six camera shapes, 64
+    log delays 1..250 and min(H, W)/2 bins each, frames generated on the GPU as the benchmark does)
+    in one batch: every member's bin and pair counts equal the oracle's, and the members of 128^2
+    and 256^2 frames match the FP64 oracle's D within 2e-5."""
+    P.build()
+    rw = S.RAGGED_WORKLOADS["ragged48"]
+    mem = rw.members()
+    frames = []
+    for (H, W, Dc, d, nq, seed) in mem:
+        src = S.OUFrameSource(H, W, Dc, seed=seed, device="cuda", dtype=torch.float32)
+        f = torch.empty((rw.N, H, W), dtype=torch.int16, device="cuda")
+        for o in range(0, rw.N, 50):
+            f[o:o + 50] = src.next_frames(min(50, rw.N - o))
+        frames.append(f)
+    torch.cuda.synchronize()
+    with P.NFSBatch([(m[0], m[1]) for m in mem], [m[3] for m in mem], [m[4] for m in mem]) as b:
+        b.push_frames_device(frames)
+        got = [b.structure_function(s) for s in range(len(mem))]
+    small = [s for s, m in enumerate(mem) if m[0] * m[1] <= 256 * 256]
+    assert len(small) >= 8
+    for s, (H, W, Dc, d, nq, seed) in enumerate(mem):
+        table = P.bin_table(H, W, nq)
+        np.testing.assert_array_equal(got[s]["bin_counts"], table["bin_counts"])
+        np.testing.assert_array_equal(got[s]["pair_counts"], [max(0, rw.N - t) for t in d])
+    for s in small:
+        H, W, Dc, d, nq, seed = mem[s]
+        ref = oracle_lib.structure_function(frames[s].cpu().numpy().view(np.uint16), d, nq)
+        np.testing.assert_array_equal(got[s]["bin_counts"], ref["bin_counts"])
+        assert rel_err(got[s], ref) <= TOL_F32, (s, H, W, rel_err(got[s], ref))
