@@ -151,6 +151,14 @@ def delay_block_bytes(delays, N, K, M):
     return total, launches, pairs
 
 
+def binned_modes(P, H, W, n_qbins, first=0, count=None):
+    """Half-plane modes that fall in a radial bin (the modes whose D the job needs), among the
+    column-major modes first .. first+count-1 (a slab's share; default all)."""
+    b = P.bin_table(H, W, n_qbins)["bin_of_mode"].T.reshape(-1)  # mode kx * H + ky
+    count = b.size if count is None else count
+    return int(np.count_nonzero(b[first:first + count] >= 0))
+
+
 def sample_shape(job_delays, target_pairs, n_max):
     """A bounded sample of the job for the oracle: its first n frames with the job's own delays
     below n (a prefix of its list), n the largest with at most target_pairs pairs (at least 2)."""
@@ -342,6 +350,12 @@ def main():
     ctx_span = ctx.get_option(P.OPT_DELAY_SPAN)
     ctx_chunk = ctx.get_option(P.OPT_FFT_CHUNK)
     M = ctx.get_option(P.OPT_SLAB_MODES)  # modes held (column-major, padded to 16-mode tiles; a slab's share)
+    # modes the delay update keeps: the 16-mode tiles holding a binned mode (the corner modes beyond
+    # the Nyquist circle are in no bin); its flops and bytes are counted on these
+    M_delay = ctx.get_option(P.OPT_DELAY_MODES)
+    # algorithmic flops count the binned modes (of this rank's slab) only; the kernel also updates
+    # the corner modes that share a 16-mode tile with a binned one, which are not counted
+    modes = binned_modes(P, w.H, w.W, w.n_qbins, ctx.get_option(P.OPT_SLAB_FIRST_MODE), M)
     # the pinned host copy for the end-to-end run, written by the CPU (as an acquisition program
     # writes frames into its buffer) through a small page-locked staging buffer.  The library's
     # host push reads it with the SMs (NFS_OPT_H2D = 0): the copy engines read the first ~4.6 GB of
@@ -400,8 +414,7 @@ def main():
     # Its arithmetic intensity (6 flops per pair and mode against each ring value and accumulator
     # moved once per block) lies above the FP32 ridge point, so the roofline that bounds it is the
     # FP32 ALU peak; the HBM fraction the metric asks for is reported beside it.
-    alg_bytes, n_launch, pairs = delay_block_bytes(w.delays, w.N, K, M)
-    modes = M if slabs else w.H * (w.W // 2 + 1)  # a slab's share of the modes on this rank
+    alg_bytes, n_launch, pairs = delay_block_bytes(w.delays, w.N, K, M_delay)
     alg_flops = FLOPS_PER_PAIR_MODE * pairs * modes
     delay_ms, delay_n = tim["delay"]
     per_launch_ms = delay_ms / max(delay_n, 1)
@@ -432,7 +445,7 @@ def main():
     # a pass moving only these bytes at the measured HBM peak would reach.
     scratch = w.H * (((w.W // 2 + 1) + 3) // 4 * 4) * 8
     stage_bytes = {"mean": w.N * w.H * w.W * 2, "rowfft": w.N * (w.H * w.W * 2 + scratch),
-                   "colfft": w.N * (scratch + M * 8), "delay": alg_bytes, "bin": len(w.delays) * M * 8}
+                   "colfft": w.N * (scratch + M * 8), "delay": alg_bytes, "bin": len(w.delays) * M_delay * 8}
     stage_gbs = {k: b / (stage_ms[k] / 1e3) / 1e9 for k, b in stage_bytes.items() if stage_ms.get(k)}
     pass_bytes = sum(stage_bytes.values())
     hbm_bound = {"bytes_per_step": pass_bytes, "frames_per_s": w.N / (pass_bytes / (hbm_peak * 1e9)),
@@ -538,6 +551,7 @@ def main():
                 "config": {"workload": w.name, "frames": w.N, "H": w.H, "W": w.W, "delays": len(w.delays),
                            "tau_max": w.delays[-1], "n_qbins": w.n_qbins, "block_frames": K,
                            "delay_span": ctx_span, "fft_chunk": ctx_chunk,
+                           "delay_modes": int(M_delay), "binned_modes": int(modes),
                            "parallelism": (f"mode-slabs{world}" if slabs else f"replicas{world}"),
                            "l2": "inputs larger than L2 (frames "
                            f"{w.N * w.H * w.W * 2 / 1e9:.1f} GB, ring "

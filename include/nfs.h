@@ -155,7 +155,9 @@ int nfs_structure_function(nfs_ctx *ctx, double *D, int64_t *bin_counts, int64_t
 
 /*
  * The 2-D spectrum D(k, tau_j) for one delay index j before binning, as FP64 [H][W/2+1]
- * (k_x fastest, k_y = 0..H-1 in FFT order).  Flushes pending frames and synchronises.
+ * (k_x fastest, k_y = 0..H-1 in FFT order).  Flushes pending frames and synchronises.  On the FP32
+ * path it needs NFS_OPT_MODES = 1, set before the first frame (otherwise NFS_ESTATE, not sticky:
+ * the delay update then keeps only the tiles the bins read).
  */
 int nfs_export_spectrum(nfs_ctx *ctx, int delay_index, double *out);
 
@@ -216,6 +218,14 @@ void *nfs_get_stream(const nfs_ctx *ctx);
                                     speed whatever state the host pages are in; the copy engines were
                                     measured at 8-38 GB/s on the first gigabytes of some freshly
                                     pinned buffers */
+#define NFS_OPT_MODES 14         /* which modes the FP32 delay update keeps: 0 = the 16-mode tiles that
+                                    hold a binned mode (default: the corner modes beyond the Nyquist
+                                    circle, |f| >= 1/2 cycle per pixel in the half-plane, which no bin
+                                    reads, are left out; about 21 % of the modes); 1 = every mode
+                                    (needed for nfs_export_spectrum).  Only before the first frame
+                                    (NFS_ESTATE after); binned results are bit-identical either way */
+#define NFS_OPT_DELAY_MODES 15   /* read-only: modes the delay update keeps (16 x tiles; all modes M of
+                                    the context when NFS_OPT_MODES = 1 or on the FP64 path) */
 #define NFS_OPT_SLAB_FIRST_MODE 10 /* read-only: first mode (column-major order) of a slab context */
 #define NFS_OPT_SLAB_MODES 11      /* read-only: modes held (the slab's share, a multiple of 16) */
 int nfs_set_option(nfs_ctx *ctx, int key, int64_t value);

@@ -42,6 +42,8 @@ OPT_SLAB_FIRST_MODE = 10
 OPT_SLAB_MODES = 11
 OPT_DELAY_SPAN = 12
 OPT_H2D = 13
+OPT_MODES = 14
+OPT_DELAY_MODES = 15
 FIT_GAUSS_NEWTON = 0
 FIT_ADAM = 1
 STAGES = ("h2d", "mean", "rowfft", "colfft", "delay", "bin")

@@ -684,11 +684,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_tiled(const float2 *_
                                                                  const __grid_constant__ DelaySchedule sched,
                                                                  float2 *__restrict__ acc, int nd,
                                                                  int *__restrict__ err, int stall_group,
-                                                                 const float2 *__restrict__ ring_cur, int R_cur)
+                                                                 const float2 *__restrict__ ring_cur, int R_cur,
+                                                                 const int *__restrict__ tiles)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     TiledSmem &S = *reinterpret_cast<TiledSmem *>(smem_raw);
-    tile_pass<PACKED>(S, ring, R, M, t0, nb, sched, sched.nst, sched.nbatch, acc, nd, err, stall_group, blockIdx.x,
+    const size_t tile = tiles ? (size_t)tiles[blockIdx.x] : (size_t)blockIdx.x;
+    tile_pass<PACKED>(S, ring, R, M, t0, nb, sched, sched.nst, sched.nbatch, acc, nd, err, stall_group, tile,
                       ring_cur, R_cur);
 }
 
@@ -710,8 +712,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_delay_f32_batched(const BatchIt
                 hi = mid - 1;
         }
         const BatchItem it = items[lo];
+        const size_t tile = it.tiles ? (size_t)it.tiles[i - it.first] : (size_t)(i - it.first);
         tile_pass<PACKED>(S, it.ring, it.R, it.M, it.t0, it.nb, *it.sched, it.nst, it.nbatch, it.acc, it.nd, err, -1,
-                          (size_t)(i - it.first));
+                          tile);
     }
 }
 
@@ -819,19 +822,20 @@ cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s)
     sc.nst = nst;
     sc.nbatch = nbatch;
     const size_t smem = sizeof(TiledSmem);
-    const unsigned grid = (unsigned)(a.M / kTile);
+    const unsigned grid = (unsigned)(a.tiles ? a.ntiles : a.M / kTile);
+    if (grid == 0) return cudaSuccess;
     if (variant == 2) {
         cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         k_delay_f32_tiled<false><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
-                                                               a.stall_group, a.ring_cur, a.R_cur);
+                                                               a.stall_group, a.ring_cur, a.R_cur, a.tiles);
     } else {
         cudaError_t e = cudaFuncSetAttribute(k_delay_f32_tiled<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
         k_delay_f32_tiled<true><<<grid, kThreads, smem, s>>>(a.ring, a.R, a.M, a.t0, a.nb, sc, a.acc, a.nd, a.err,
-                                                              a.stall_group, a.ring_cur, a.R_cur);
+                                                              a.stall_group, a.ring_cur, a.R_cur, a.tiles);
     }
     return cudaGetLastError();
 }

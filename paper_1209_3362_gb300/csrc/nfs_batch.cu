@@ -80,6 +80,8 @@ static int batch_flush(nfs_batch *b, bool all)
             it.ring = (const float2 *)c->d_ring;
             it.acc = (float2 *)c->d_acc;
             it.sched = b->d_scheds + s;
+            it.tiles = c->modes_all ? nullptr : c->d_tiles;
+            it.ntiles = c->modes_all ? (long long)(c->g.M / kTile) : c->n_tiles_binned;
             it.t0 = c->nprocessed;
             it.first = total;
             it.M = c->g.M;
@@ -88,8 +90,8 @@ static int batch_flush(nfs_batch *b, bool all)
             it.nd = c->nd;
             it.nst = nst;
             it.nbatch = nbatch;
-            b->items.push_back(it);
-            total += (long long)(c->g.M / kTile);
+            if (it.ntiles > 0) b->items.push_back(it);
+            total += it.ntiles;
         }
         c->nprocessed = c->nframes;
     }

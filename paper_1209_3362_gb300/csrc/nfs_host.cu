@@ -169,6 +169,7 @@ int build_bins(nfs_ctx *c)
     std::vector<int> bin_of;
     bin_table(H, W, nq, &bin_of, &c->counts, &c->qmean);
     std::vector<std::vector<int>> lists((size_t)nq);
+    std::vector<char> binned_tile(c->g.M / kTile, 0);
     for (int ky = 0; ky < H; ++ky)
         for (int kx = 0; kx < Wh; ++kx) {
             const int b = bin_of[(size_t)ky * Wh + kx];
@@ -177,7 +178,15 @@ int build_bins(nfs_ctx *c)
             if (kl < 0 || kl >= (long long)c->g.M) continue;
             const int two = (kx != 0 && kx != W / 2) ? 1 : 0;
             lists[b].push_back((int)((kl << 1) | two));
+            binned_tile[(size_t)kl / kTile] = 1;
         }
+    std::vector<int> tiles;
+    for (size_t t = 0; t < binned_tile.size(); ++t)
+        if (binned_tile[t]) tiles.push_back((int)t);
+    c->n_tiles_binned = (long long)tiles.size();
+    CK(c, cudaMalloc(&c->d_tiles, sizeof(int) * std::max<size_t>(tiles.size(), 1)));
+    if (!tiles.empty())
+        CK(c, cudaMemcpy(c->d_tiles, tiles.data(), sizeof(int) * tiles.size(), cudaMemcpyHostToDevice));
     std::vector<int> off((size_t)nq + 1, 0), modes;
     for (int b = 0; b < nq; ++b) off[b + 1] = off[b] + (int)lists[b].size();
     modes.reserve((size_t)off[nq]);
@@ -225,6 +234,7 @@ void free_all(nfs_ctx *c)
     cudaFree(c->d_scratch);
     cudaFree(c->d_bin_off);
     cudaFree(c->d_bin_modes);
+    cudaFree(c->d_tiles);
     cudaFree(c->d_pairs);
     cudaFree(c->d_counts);
     cudaFree(c->d_D);
@@ -277,6 +287,10 @@ int flush_block(nfs_ctx *c)
     if (c->cross) {
         a.ring_cur = (const float2 *)c->d_ring_cur;
         a.R_cur = c->K;
+    }
+    if (!c->modes_all) {
+        a.tiles = c->d_tiles;
+        a.ntiles = (size_t)c->n_tiles_binned;
     }
     rc = timed(c, NFS_STAGE_DELAY, c->stream, [&] { return launch_delay_f32(a, c->delay_variant, c->stream); },
                "delay_f32");
@@ -878,6 +892,11 @@ int nfs_export_spectrum(nfs_ctx *c, int j, double *out)
     int rc = enter(c);
     if (rc) return rc;
     if (!out || j < 0 || j >= c->nd) return NFS_EINVAL;
+    // the FP32 path updates only the tiles the bins read unless every mode was asked for
+    if (c->f32() && !c->modes_all) {
+        c->errmsg = "nfs_export_spectrum: the 2-D spectrum needs NFS_OPT_MODES = 1 before the first frame";
+        return NFS_ESTATE;  // not sticky: the context stays usable
+    }
     if ((rc = flush_block(c))) return rc;
     const size_t n = (size_t)c->g.H * c->g.Wh;
     if (!c->d_export && (rc = alloc_dev(c, (void **)&c->d_export, sizeof(double) * n))) return rc;
@@ -976,6 +995,11 @@ int nfs_set_option(nfs_ctx *c, int key, int64_t v)
             if (v < 0 || v > 1) return NFS_EINVAL;
             c->h2d = (int)v;
             return NFS_OK;
+        case NFS_OPT_MODES:
+            if (v < 0 || v > 1) return NFS_EINVAL;
+            if (c->nframes > 0) return NFS_ESTATE;  // earlier blocks would lack the other modes
+            c->modes_all = (int)v;
+            return NFS_OK;
         case NFS_OPT_DELAY_SPAN:
             if (v == 0) {
                 if (c->nframes > 0 || c->have_ref) return NFS_ESTATE;
@@ -1004,6 +1028,10 @@ int nfs_get_option(const nfs_ctx *c, int key, int64_t *v)
         case NFS_OPT_SLAB_MODES: *v = (int64_t)c->g.M; return NFS_OK;
         case NFS_OPT_DELAY_SPAN: *v = c->span; return NFS_OK;
         case NFS_OPT_H2D: *v = c->h2d; return NFS_OK;
+        case NFS_OPT_MODES: *v = c->modes_all; return NFS_OK;
+        case NFS_OPT_DELAY_MODES:
+            *v = (c->f32() && !c->modes_all) ? c->n_tiles_binned * kTile : (int64_t)c->g.M;
+            return NFS_OK;
         default: return NFS_EINVAL;
     }
 }

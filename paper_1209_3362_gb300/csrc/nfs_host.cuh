@@ -93,6 +93,11 @@ struct nfs_ctx {
     float2 *d_scratch = nullptr;                         // FP32 row-pass output, kMaxChunkF32 frames
     nfs::FftPlan plan_row, plan_col;
     int *d_bin_off = nullptr, *d_bin_modes = nullptr;
+    // The 16-mode tiles that hold a binned mode (ascending): the FP32 delay update runs on these
+    // only unless every mode is asked for (NFS_OPT_MODES = 1, which the 2-D export needs).
+    int *d_tiles = nullptr;
+    long long n_tiles_binned = 0;
+    int modes_all = 0;
     long long *d_pairs = nullptr, *d_counts = nullptr;
     double *d_D = nullptr, *d_export = nullptr;
     nfs::DelaySchedule *sched = nullptr;  // tiled-kernel schedule (host copy, passed by value); NULL if too long

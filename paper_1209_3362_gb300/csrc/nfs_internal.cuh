@@ -188,17 +188,24 @@ struct DelayArgs {
     // at delay d is (block frame t, ring frame t - d), d = 0 included.  NULL: one ring for both.
     const float2 *ring_cur = nullptr;
     int R_cur = 0;
+    // Tiles to update (16-mode tile indices, ascending; the tiled kernels only): NULL = every tile.
+    // A context lists the tiles that hold a binned mode, so the corner modes beyond the Nyquist
+    // circle, which no bin reads, are not updated.
+    const int *tiles = nullptr;
+    size_t ntiles = 0;
 };
 cudaError_t launch_delay_f32(const DelayArgs &a, int variant, cudaStream_t s);
 
-// One work item of the ragged batch: the block t0 .. t0+nb-1 of one sequence, tiles
-// first .. first+M/32-1 of the launch.
+// One work item of the ragged batch: the block t0 .. t0+nb-1 of one sequence, work tiles
+// first .. first+ntiles-1 of the launch (its tiles[0 .. ntiles), or tiles 0 .. ntiles-1).
 struct BatchItem {
     const float2 *ring;
     float2 *acc;
     const DelaySchedule *sched;  // device copy
+    const int *tiles;            // the tiles to update (NULL: tiles 0 .. ntiles-1)
     long long t0;
     long long first;
+    long long ntiles;
     size_t M;
     int R, nb, nd, nst, nbatch;
 };

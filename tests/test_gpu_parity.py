@@ -122,6 +122,7 @@ def test_empty_and_single_frame(oracle_lib, path):
     fr = S.OUFrameSource(H, W, 1.0, seed=5).frames_numpy(3)
     _, counts, _ = oracle_lib.bins(H, W, nq)
     with P.NFS(H, W, delays, nq, path=path) as ctx:
+        ctx.set_option(P.OPT_MODES, 1)  # every mode: the 2-D export below
         r0 = ctx.structure_function()
         assert np.all(r0["D"] == 0.0) and list(r0["pair_counts"]) == [0, 0, 0]
         np.testing.assert_array_equal(r0["bin_counts"], counts)
@@ -184,6 +185,7 @@ def test_export_spectrum_matches_oracle_2d(oracle_lib):
     delays = [1, 4, 13]
     ref = oracle_lib.structure_function(fr, delays, 16, want_2d=True)
     with P.NFS(32, 48, delays, 16) as ctx:
+        ctx.set_option(P.OPT_MODES, 1)
         ctx.push_frames(fr)
         for j in range(len(delays)):
             got = ctx.export_spectrum(j)
@@ -287,6 +289,7 @@ def test_full_size_2048_sampled_modes(oracle_lib):
     with P.NFS(H, W, delays, nq) as ctx:
         K = ctx.get_option(P.OPT_BLOCK_FRAMES)
         assert K == 512 and ctx.get_option(P.OPT_FFT_CHUNK) == 32 and N >= delays[-1] + K  # a steady block
+        ctx.set_option(P.OPT_MODES, 1)
         ctx.push_frames_device(torch.from_numpy(fr.view(np.int16)).cuda())
         got = ctx.structure_function()
         spectra = {j: ctx.export_spectrum(j) for j in (0, 1, 4, 6)}
@@ -341,6 +344,7 @@ def test_max_frame_size(oracle_lib, H, W, path):
     delays = [1, 2, 7, 23]
     fr = S.OUFrameSource(H, W, 1.5, seed=4096 + W, device="cuda", dtype=torch.float32).frames_numpy(N)
     with P.NFS(H, W, delays, nq, path=path, block_frames=64 if path == "f32" else 0) as ctx:
+        ctx.set_option(P.OPT_MODES, 1)
         ctx.push_frames(fr)
         got = ctx.structure_function()
         spectra = {j: ctx.export_spectrum(j) for j in range(len(delays))}
@@ -446,3 +450,44 @@ def test_delay_span_autotune_and_explicit_spans_are_bit_identical():
                 ctx.set_option(P.OPT_DELAY_SPAN, 15)
     for span, r in results.items():
         np.testing.assert_array_equal(r["D"], results[None]["D"], err_msg=str(span))
+
+
+def test_binned_modes_only_by_default(oracle_lib):
+    """By default the FP32 delay update keeps only the 16-mode tiles that hold a binned mode (the
+    corner modes beyond the Nyquist circle are in no bin): the binned result is bit-identical to a
+    context that keeps every mode, the 2-D export asks for every mode, and the choice is made before
+    the first frame.  Also checked on a slab context."""
+    H, W, nq = 96, 128, 24
+    fr = S.OUFrameSource(H, W, 1.2, seed=77).frames_numpy(700)
+    delays = [1, 2, 3, 9, 40, 333]
+    out = {}
+    for modes in (0, 1):
+        with P.NFS(H, W, delays, nq) as ctx:
+            assert ctx.get_option(P.OPT_MODES) == 0
+            ctx.set_option(P.OPT_MODES, modes)
+            M = ctx.get_option(P.OPT_SLAB_MODES)
+            kept = ctx.get_option(P.OPT_DELAY_MODES)
+            assert (kept == M) if modes else (kept % 16 == 0 and 0.75 * M < kept < 0.9 * M)
+            ctx.push_frames(fr[:300])
+            with pytest.raises(P.NFSError) as e:
+                ctx.set_option(P.OPT_MODES, 1 - modes)
+            assert e.value.status == P.NFS_ESTATE
+            ctx.push_frames(fr[300:])
+            out[modes] = ctx.structure_function()
+            if modes == 0:
+                with pytest.raises(P.NFSError) as e:
+                    ctx.export_spectrum(0)
+                assert e.value.status == P.NFS_ESTATE
+                assert ctx.structure_function()["pair_counts"][0] == 699  # the context is still usable
+    np.testing.assert_array_equal(out[0]["D"], out[1]["D"])
+    ref = oracle_lib.structure_function(fr, delays, nq)
+    check_counts(out[0], ref)
+    assert rel_err(out[0], ref) <= TOL_F32
+    with P.NFS(H, W, delays, nq, slab=1, n_slabs=3) as c:
+        c.push_frames(fr)
+        slab = c.structure_function()
+    with P.NFS(H, W, delays, nq, slab=1, n_slabs=3) as c:
+        c.set_option(P.OPT_MODES, 1)
+        c.push_frames(fr)
+        np.testing.assert_array_equal(c.structure_function()["D"], slab["D"])
+

@@ -18,6 +18,7 @@ def test_slabs_add_up_to_the_whole_context(H, W, n_slabs):
     fr = S.OUFrameSource(H, W, 1.1, seed=H + n_slabs).frames_numpy(640)
     delays, nq = [1, 2, 3, 4, 5, 17, 100, 300, 530], 32
     with P.NFS(H, W, delays, nq) as whole:
+        whole.set_option(P.OPT_MODES, 1)  # every mode: the 2-D exports compared below
         whole.push_frames(fr)
         ref = whole.structure_function()
         ex_ref = whole.export_spectrum(6)
@@ -27,6 +28,7 @@ def test_slabs_add_up_to_the_whole_context(H, W, n_slabs):
         with P.NFS(H, W, delays, nq, slab=s, n_slabs=n_slabs) as c:
             first, n = P.slab_range(H, W, s, n_slabs)
             assert (c.get_option(P.OPT_SLAB_FIRST_MODE), c.get_option(P.OPT_SLAB_MODES)) == (first, n)
+            c.set_option(P.OPT_MODES, 1)
             if s % 2:
                 c.push_frames(fr[:333])
                 c.push_frames(fr[333:])
