@@ -62,8 +62,8 @@ FLOPS_PER_PAIR_MODE = 6      # |P_t - P_s|^2 accumulated: 2 subtractions, 2 squa
 # (dram__bytes_read.sum + dram__bytes_write.sum of a steady-state launch; see profiles/).  It
 # applies only to the kernel source it was measured on: any change to these files voids it.
 DELAY_KERNEL_SOURCES = ("paper_1209_3362_gb300/csrc/k_delay.cu", "paper_1209_3362_gb300/csrc/nfs_internal.cuh")
-NCU_DELAY_CALIBRATION = {"sha256": "90888fcd05bc52baf8de254a0f07f162f5f7dca3b6e77282cee26cecbfeddcd9",
-                         "dram_bytes_per_alg_byte": 0.9962}
+NCU_DELAY_CALIBRATION = {"sha256": "977ae1a322a26a3cc567a51471d406befaa099aa1c79e8ffe88099503fee14cc",
+                         "dram_bytes_per_alg_byte": 0.9950}
 
 
 def delay_kernel_sha():
