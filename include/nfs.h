@@ -120,7 +120,8 @@ int nfs_bin_table(int H, int W, int n_qbins, int32_t *bin_of_mode, int64_t *bin_
  * call returns, so the caller may reuse the buffer at once; the analysis itself runs
  * asynchronously on the context's stream.  Page-locked buffers are read directly (by the SMs or
  * the copy engines: NFS_OPT_H2D); pageable ones pass through the context's pinned staging buffers.
- * The copies run on a stream of the device's greatest priority, chunks of up to 256 MB into a
+ * Read by the SMs, whole frames also have their exact sums taken during the copy (no separate sum
+ * pass).  The copies run on a stream of the device's greatest priority, chunks of up to 256 MB into a
  * device staging ring of two delay blocks; a slot transformed into the spectrum ring is handed
  * back just before the next delay launch, so that its refill runs beside that launch.
  * A frame whose pixels sum to 0 has no mean: its normalised image is taken as 0.

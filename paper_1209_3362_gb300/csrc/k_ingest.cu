@@ -48,6 +48,67 @@ cudaError_t launch_gather_h2d(const void *host_src, void *dst, size_t bytes, cud
     return cudaGetLastError();
 }
 
+// Host-to-device copy of nf whole frames (f16 16-byte pieces each) read by the SMs, adding each
+// frame's exact pixel sum into sums[f] on the way (the frames pass through the SMs anyway, so the
+// separate sum pass over device memory is saved): cpf CTAs per frame, one 64-bit atomic per CTA.
+__device__ __forceinline__ unsigned sum_u16x8(uint4 v)
+{
+    return (v.x & 0xffffu) + (v.x >> 16) + (v.y & 0xffffu) + (v.y >> 16) + (v.z & 0xffffu) + (v.z >> 16) +
+           (v.w & 0xffffu) + (v.w >> 16);
+}
+
+__global__ void __launch_bounds__(kGatherThreads) k_gather_h2d_sums(const uint4 *__restrict__ src,
+                                                                    uint4 *__restrict__ dst, size_t f16, int cpf,
+                                                                    unsigned long long *__restrict__ sums)
+{
+    const int f = blockIdx.x / cpf, part = blockIdx.x % cpf;
+    const uint4 *s = src + (size_t)f * f16;
+    uint4 *d = dst + (size_t)f * f16;
+    const size_t stride = (size_t)cpf * blockDim.x;
+    size_t i = (size_t)part * blockDim.x + threadIdx.x;
+    unsigned long long acc = 0;
+    for (; i + 3 * stride < f16; i += 4 * stride) {
+        const uint4 a = s[i], b = s[i + stride], c = s[i + 2 * stride], e = s[i + 3 * stride];
+        d[i] = a;
+        d[i + stride] = b;
+        d[i + 2 * stride] = c;
+        d[i + 3 * stride] = e;
+        acc += (unsigned long long)(sum_u16x8(a) + sum_u16x8(b)) + (sum_u16x8(c) + sum_u16x8(e));
+    }
+    for (; i < f16; i += stride) {
+        const uint4 a = s[i];
+        d[i] = a;
+        acc += sum_u16x8(a);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __shared__ unsigned long long ws[kGatherThreads / 32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+#pragma unroll
+        for (int w = 0; w < kGatherThreads / 32; ++w) t += ws[w];
+        atomicAdd(&sums[f], t);
+    }
+}
+
+cudaError_t launch_gather_h2d_sums(const void *host_src, void *dst, int nf, size_t frame_bytes,
+                                   unsigned long long *sums, cudaStream_t s)
+{
+    if (nf <= 0) return cudaSuccess;
+    if (((reinterpret_cast<uintptr_t>(host_src) | reinterpret_cast<uintptr_t>(dst) | frame_bytes) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const cudaError_t carve =
+        cudaFuncSetAttribute(k_gather_h2d_sums, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (carve != cudaSuccess) return carve;
+    const int cpf = std::max(1, kGatherCtas / nf);
+    k_gather_h2d_sums<<<(unsigned)(nf * cpf), kGatherThreads, 0, s>>>(reinterpret_cast<const uint4 *>(host_src),
+                                                                       reinterpret_cast<uint4 *>(dst), frame_bytes / 16,
+                                                                       cpf, sums);
+    return cudaGetLastError();
+}
+
 // sums[blockIdx.y] += sum of the frame's pixels.  Integer arithmetic, so the result is exact and
 // independent of the order of the atomic adds.  VEC: 16-byte loads (frame start 16-byte aligned).
 template <bool VEC>

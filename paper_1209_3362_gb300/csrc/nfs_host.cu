@@ -221,6 +221,7 @@ void free_all(nfs_ctx *c)
         if (c->ev_hcopied[i]) cudaEventDestroy(c->ev_hcopied[i]);
     }
     cudaFree(c->d_sums);
+    cudaFree(c->d_slot_sums);
     cudaFree(c->d_ref);
     cudaFree(c->d_ring);
     cudaFree(c->d_ring_cur);
@@ -308,6 +309,12 @@ int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums
     int rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] { return launch_frame_sums(dsrc, n, c->g, sums, c->stream); },
                    "frame_sums");
     if (rc) return rc;
+    return reference_once(c, dsrc, n, sums);
+}
+
+int reference_once(nfs_ctx *c, const uint16_t *dsrc, int n, const unsigned long long *sums)
+{
+    int rc = NFS_OK;
     if (!c->have_ref && c->f32()) {
         rc = timed(c, NFS_STAGE_MEAN, c->stream, [&] {
             char *base = reinterpret_cast<char *>(c->d_ref);
@@ -606,6 +613,8 @@ int create_impl(int H, int W, const int32_t *delays, int n_delays, int n_qbins, 
             return bail(NFS_ECUDA);
     for (int i = 0; i < 2; ++i)
         if (cudaEventCreateWithFlags(&c->ev_hcopied[i], cudaEventDisableTiming) != cudaSuccess) return bail(NFS_ECUDA);
+    if ((rc = alloc_dev(c, (void **)&c->d_slot_sums, sizeof(unsigned long long) * (size_t)c->copy_frames * c->n_slots)))
+        return bail(rc);
     if ((rc = alloc_dev(c, (void **)&c->d_stage, c->frame_bytes() * (size_t)c->copy_frames * c->n_slots)))
         return bail(rc);
     const size_t ring_bytes = (size_t)c->R * c->g.M * c->csize();
@@ -794,17 +803,28 @@ int nfs_push_frames(nfs_ctx *c, const uint16_t *h, int n)
             memcpy(c->h_stage[hs], src, bytes);
             src = c->h_stage[hs];
         }
+        // The SM copy of whole page-locked frames also takes their sums (into the slot's own sums, which
+        // the transforms of this slot read before it is handed back); otherwise a sum pass follows.
+        unsigned long long *ssum = c->d_slot_sums + (size_t)slot * c->copy_frames;
+        const void *dev = nullptr;
+        const bool fused = c->h2d == 0 && (c->frame_bytes() & 15) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0 &&
+                           (reinterpret_cast<uintptr_t>(src) & 15) == 0 && (dev = host_device_view(src)) != nullptr;
         rc = timed(c, NFS_STAGE_H2D, c->copy_stream, [&] {
-            return copy_h2d(dst, src, bytes, c->copy_stream, c->h2d == 0, &c->launches);
+            if (!fused) return copy_h2d(dst, src, bytes, c->copy_stream, c->h2d == 0, &c->launches);
+            cudaError_t e = cudaMemsetAsync(ssum, 0, sizeof(unsigned long long) * (size_t)nc, c->copy_stream);
+            if (e == cudaSuccess) e = launch_gather_h2d_sums(dev, dst, nc, c->frame_bytes(), ssum, c->copy_stream);
+            if (e == cudaSuccess) ++c->launches;
+            return e;
         }, "h2d");
         if (rc) return rc;
         if (hs >= 0) CK(c, cudaEventRecord(c->ev_hcopied[hs], c->copy_stream));
         CK(c, cudaEventRecord(c->ev_filled[slot], c->copy_stream));
         CK(c, cudaStreamWaitEvent(c->stream, c->ev_filled[slot], 0));
-        if ((rc = frame_sums(c, dst, nc, c->d_sums))) return rc;
+        unsigned long long *sums = fused ? ssum : c->d_sums;
+        if ((rc = fused ? reference_once(c, dst, nc, sums) : frame_sums(c, dst, nc, sums))) return rc;
         for (int o = 0; o < nc;) {
             const int nf = next_chunk(c, nc - o, c->fft_chunk);
-            rc = process_chunk(c, dst + (size_t)o * c->g.HW, nf, false, c->d_sums + o);
+            rc = process_chunk(c, dst + (size_t)o * c->g.HW, nf, false, sums + o);
             if (rc) return rc;
             o += nf;
         }

@@ -10,6 +10,13 @@
 #include "nfs_internal.cuh"
 
 namespace nfs {
+// Copy of nf whole frames of frame_bytes each from page-locked host memory, read by the SMs like
+// launch_gather_h2d, adding frame f's exact pixel sum into sums[f] (zeroed by the caller);
+// cudaErrorInvalidValue (nothing launched) unless both addresses and frame_bytes are multiples of
+// 16 bytes.  (k_ingest.cu)
+cudaError_t launch_gather_h2d_sums(const void *host_src, void *dst, int nf, size_t frame_bytes,
+                                   unsigned long long *sums, cudaStream_t s);
+
 namespace host {
 
 // A named NVTX range over a scope: the C ABI's entry points appear as ranges in a profiler's
@@ -74,6 +81,7 @@ struct nfs_ctx {
     // through two pinned host chunks first.
     int copy_frames = 1, n_slots = 2;
     uint16_t *d_stage = nullptr;
+    unsigned long long *d_slot_sums = nullptr;  // per staging slot: its frames' sums (host pushes)
     // Staging slots whose frames are transformed but whose release (ev_free) is held back until
     // just before the next delay launch, so that the copies refilling them overlap that launch
     // (where one copy CTA fits beside each delay CTA) instead of the transforms of the next block.
@@ -177,6 +185,8 @@ int timed(nfs_ctx *c, int stage, cudaStream_t s, F &&f, const char *what)
 int flush_block(nfs_ctx *c);
 int release_slots(nfs_ctx *c);
 int frame_sums(nfs_ctx *c, const uint16_t *dsrc, int n, unsigned long long *sums);
+// The reference image from n device frames with known sums, the first time a context sees frames.
+int reference_once(nfs_ctx *c, const uint16_t *dsrc, int n, const unsigned long long *sums);
 int process_chunk(nfs_ctx *c, const uint16_t *dsrc, int nf, bool old, const unsigned long long *sums);
 int autotune_fft_chunk(nfs_ctx *c);
 int set_delay_span(nfs_ctx *c, int span);

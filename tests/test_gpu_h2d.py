@@ -1,6 +1,7 @@
-"""Host pushes: the SMs' copy kernel (NFS_OPT_H2D = 0, the default) and the copy engines
-(NFS_OPT_H2D = 1) move the same bytes, so the structure functions are bit-identical; a pinned
-source that is not 16-byte aligned falls back to the copy engines with the same result."""
+"""Host pushes: the SMs' copy kernel (NFS_OPT_H2D = 0, the default), which also takes the frames'
+exact sums on the way, and the copy engines (NFS_OPT_H2D = 1) followed by the sum kernel give the
+same sums and the same bytes, so the structure functions are bit-identical; a pinned source that
+is not 16-byte aligned falls back to the copy engines with the same result."""
 import numpy as np
 import pytest
 
@@ -13,13 +14,15 @@ DELAYS = [1, 2, 3, 17, 300]
 
 
 def _run(P, frames, h2d, split=(0, 300, 700)):
+    """Result and the launches of the mean stage (sum kernels and the one reference image)."""
     with P.NFS(H, W, DELAYS, 16) as c:
         c.set_option(P.OPT_H2D, h2d)
         assert c.get_option(P.OPT_H2D) == h2d
+        c.set_option(P.OPT_TIMING, 1)
         for a, b in zip(split[:-1], split[1:]):
             c.push_frames(frames[a:b])
         r = c.structure_function()
-        return r, c.launch_count
+        return r, c.timings()["mean"][1]
 
 
 @pytest.mark.gpu
@@ -32,8 +35,9 @@ def test_sm_reads_and_copy_engines_are_bit_identical():
     r_ce, n_ce = _run(P, pinned, 1)
     np.testing.assert_array_equal(r_sm["D"], r_ce["D"])
     np.testing.assert_array_equal(r_sm["pair_counts"], r_ce["pair_counts"])
-    # the SM transport adds one copy-kernel launch per staged chunk; the copy engines add none
-    assert n_sm > n_ce
+    # the SM copy kernel takes the sums itself: the mean stage is the reference image alone, while
+    # the copy engines' chunks each need a sum launch
+    assert n_sm == 1 and n_ce > 1
     # pageable sources pass through the library's own pinned chunks, then the same kernel
     r_pg, n_pg = _run(P, fr, 0)
     np.testing.assert_array_equal(r_pg["D"], r_ce["D"])
