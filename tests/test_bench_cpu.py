@@ -53,3 +53,21 @@ def test_reference_arm_prints_its_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["config"]["workload"] == "ddm128"
+
+
+def test_binned_modes_equal_the_oracle_bin_table():
+    """The roofline's flops count the binned modes only: the count equals the oracle's bin table
+    (modes with a bin), and a slab's counts add up to the whole frame's."""
+    import numpy as np
+    import oracle
+    import paper_1209_3362_gb300 as P
+    oracle.build()
+    P.load_library()
+    for H, W, nq in [(64, 96, 24), (128, 128, 64), (96, 64, 40)]:
+        bin_of, _, _ = oracle.bins(H, W, nq)
+        want = int(np.count_nonzero(np.asarray(bin_of) >= 0))
+        assert bench.binned_modes(P, H, W, nq) == want
+        M = H * (W // 2 + 1)
+        parts = [bench.binned_modes(P, H, W, nq, first, n) for first, n in
+                 (P.slab_range(H, W, s, 3) for s in range(3))]
+        assert sum(parts) == want and 0.7 * M < want < 0.85 * M
